@@ -1,0 +1,236 @@
+"""Pins of the oracle's collision (Eq. SMRT), frames (binomial transform) and rebuild (Eq. fi)."""
+import numpy as np
+import pytest
+from numpy.polynomial.hermite_e import hermegauss
+
+import synthetic
+from oracle import hermite as H
+from oracle import lattice as L
+from oracle import smrt as S
+from oracle import tensors as T
+from _golden import frac, rows
+
+CASES = [("D3Q39", 3), ("D3Q103", 4), ("D3Q103", 3)]
+
+
+@pytest.fixture(scope="module")
+def lats():
+    return {n: L.by_name(n) for n in ("D3Q39", "D3Q103")}
+
+
+def _random_state(lat, N, ncell=7, seed=1, eps=0.05):
+    rng = np.random.default_rng(seed)
+    rho = 0.8 + 0.4 * rng.random(ncell)
+    u = 0.3 * rng.standard_normal((3, ncell))
+    th = 0.7 + 0.6 * rng.random(ncell)
+    feq = S.equilibrium(rho, u, th, lat, N)
+    f = feq * (1.0 + eps * rng.standard_normal(feq.shape))
+    return f, feq
+
+
+def test_table4_ratios_match_golden():
+    for model, n, m, r in rows("table4_relaxation.txt"):
+        table = S.TAU_STAR_SMRT if model == "SMRT" else S.TAU_STAR_SHAKHOV
+        assert abs(table[(int(n), int(m))] - float(frac(r))) < 1e-15
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_route_a_equals_route_b(lats, name, N):
+    """Direct local projection = absolute projection followed by the binomial transform."""
+    lat = lats[name]
+    f, _ = _random_state(lat, N, eps=0.2)
+    rho, u, th = S.conserved(f, lat)
+    dA = S.local_direct(f, lat, N, u, th)
+    dB = S.to_local(S.absolute(f, lat, N), N, u, th)
+    np.testing.assert_allclose(dA, dB, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(S.to_absolute(dB, N, u, th), S.absolute(f, lat, N), atol=1e-13)
+    # d^(0) = rho, d^(1) = 0, tr d^(2) = 0 (theta is the full 3-dof kinetic temperature)
+    np.testing.assert_allclose(dA[0], rho, rtol=1e-14)
+    np.testing.assert_allclose(dA[1:4], 0.0, atol=1e-13)
+    np.testing.assert_allclose(dA[4] + dA[7] + dA[9], 0.0, atol=1e-13)
+
+
+def test_equilibrium_coefficients_against_numerical_integration():
+    """Appendix B: a^(n) of a 1D Maxwellian equals its Hermite projection by quadrature."""
+    x, wq = hermegauss(80)                     # integrates p(x) exp(-x^2/2) exactly, deg <= 159
+    wq = wq / np.sqrt(2 * np.pi)
+    for u, th in [(0.0, 1.0), (0.7, 0.6), (-1.1, 1.4), (0.3, 1.9)]:
+        ratio = np.exp(x * x / 2 - (x - u) ** 2 / (2 * th)) / np.sqrt(th)   # f / omega
+        he = H.he_1d(8, x)
+        for n in range(9):
+            want = np.sum(wq * ratio * he[n])
+            got = S.g_coef(n, u, th)
+            assert abs(got - want) < 1e-9 * max(1.0, abs(want)), (u, th, n)
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_discrete_equilibrium_has_maxwellian_moments(lats, name, N):
+    """sum_i f^eq_i xi^alpha = integral of the Maxwellian times xi^alpha for |alpha| <= N."""
+    lat = lats[name]
+    rho, u, th = np.array([1.3]), np.array([[0.4], [-0.2], [0.1]]), np.array([0.85])
+    f = S.equilibrium(rho, u, th, lat, N)[:, 0]
+    x, wq = hermegauss(40)
+    wq = wq / np.sqrt(2 * np.pi)
+    for a in H.multi_indices_upto(N):
+        got = np.sum(f * np.prod(lat.xi ** np.array(a), axis=1))
+        want = rho[0]
+        for k in range(3):     # 1D moment of N(u_k, th): integrate (u + sqrt(th) x)^a dN(0,1)
+            want *= np.sum(wq * (u[k, 0] + np.sqrt(th[0]) * x) ** a[k])
+        assert abs(got - want) < 1e-12 * max(1, abs(want)), a
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_collision_conserves_mass_momentum_energy(lats, name, N):
+    lat = lats[name]
+    f, _ = _random_state(lat, N, eps=0.3)
+    model = S.Model(lat, N, tau_ref=0.7)
+    h = S.collide(f, model)
+    for x0, x1 in zip(S.conserved(f, lat), S.conserved(h, lat)):
+        np.testing.assert_allclose(x1, x0, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_equilibrium_is_fixed_point(lats, name, N):
+    lat = lats[name]
+    _, feq = _random_state(lat, N)
+    h = S.collide(feq, S.Model(lat, N, tau_ref=1.3))
+    np.testing.assert_allclose(h, feq, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_equal_times_reduce_to_regularised_bgk(lats, name, N):
+    """Sec. 3: all tau equal gives BGK, here f' = f^eq,N + (1 - 1/tau) Pi_N (f - f^eq,N).
+
+    Pi_N is the absolute-frame Hermite projection truncated at N written out directly from
+    Eqs. an and fi: no frames, no binomial transform, no irreducible projectors.
+    """
+    lat = lats[name]
+    f, _ = _random_state(lat, N, eps=0.2)
+    tau_c = 0.9
+    model = S.Model(lat, N, tau_ref=tau_c, tau_star={k: 1.0 for k in S.TAU_STAR_SMRT},
+                    maxwell_law=False)
+    rho, u, th = S.conserved(f, lat)
+    feq = S.equilibrium(rho, u, th, lat, N)
+    al = H.multi_indices_upto(N)
+    He = H.he_multi(al, lat.xi)
+    fact = np.array([H.alpha_factorial(a) for a in al], dtype=float)
+    proj = lat.w[:, None] * (He / fact) @ (He.T @ (f - feq))
+    want = feq + (1.0 - 1.0 / (tau_c + 0.5)) * proj
+    np.testing.assert_allclose(S.collide(f, model), want, atol=1e-13)
+
+
+def _pure_mode(n, m, rng):
+    """A random pure irreducible mode A delta^m of order n, built from Appendix A's formulas."""
+    d = np.eye(3)
+    if n - 2 * m == 0:
+        core = np.array(1.0)
+    elif n - 2 * m == 1:
+        core = rng.standard_normal(3)
+    else:
+        r = n - 2 * m
+        X = T.sym(rng.standard_normal((3,) * r))
+        if r == 2:
+            core = X - np.trace(X) / 3 * d
+        elif r == 3:
+            core = X - 3 / 5 * T.sprod(d, T.trace(X))
+        elif r == 4:
+            core = (X - 6 / 7 * T.sprod(d, T.trace(X))
+                    + 3 / 35 * T.sprod(T.delta_power(2), T.trace_pow(X, 2)))
+        else:
+            raise ValueError(r)
+    return T.sprod(core, T.delta_power(m)) if m else core
+
+
+@pytest.mark.parametrize("name,N,n,m", [("D3Q39", 3, 2, 0), ("D3Q39", 3, 3, 0), ("D3Q39", 3, 3, 1),
+                                         ("D3Q103", 4, 2, 0), ("D3Q103", 4, 3, 0), ("D3Q103", 4, 3, 1),
+                                         ("D3Q103", 4, 4, 0), ("D3Q103", 4, 4, 1), ("D3Q103", 4, 4, 2)])
+def test_single_mode_decays_at_its_own_rate(lats, name, N, n, m):
+    """Eq. SMRT: a pure (n, m) mode on a moving, non-unit-temperature state is multiplied by
+    exactly 1 - 1/tau_nm per collision, all other coefficients untouched (Galilean invariant)."""
+    lat = lats[name]
+    rng = np.random.default_rng(10 * n + m)
+    rho, u, th = 1.1, np.array([0.35, -0.2, 0.15]), 0.9
+    mode = _pure_mode(n, m, rng)
+    comp = H.components(mode)
+    al = H.multi_indices_upto(N)
+    d = np.zeros((len(al), 1))
+    d[0, 0] = rho
+    eps = 1e-3
+    for k, a in enumerate(al):
+        if sum(a) == n:
+            d[k, 0] = eps * comp[a]
+    a_abs = S.to_absolute(d, N, u[:, None], np.array([th]))
+    f = S.rebuild(a_abs, lat, N)
+    r0, u0, t0 = S.conserved(f, lat)
+    np.testing.assert_allclose([r0[0], t0[0]], [rho, th], rtol=1e-13)
+    np.testing.assert_allclose(u0[:, 0], u, atol=1e-13)
+    model = S.Model(lat, N, tau_ref=0.8)
+    h = S.collide(f, model)
+    d_after = S.local_direct(h, lat, N, u0, t0)
+    tau = S.tau_discrete(model, np.array([rho]))[(n, m)][0]
+    want = d.copy()
+    want[1:, 0] *= 0.0
+    for k, a in enumerate(al):
+        if sum(a) == n:
+            want[k, 0] = (1.0 - 1.0 / tau) * d[k, 0]
+    want[0, 0] = rho
+    np.testing.assert_allclose(d_after, want, atol=1e-14)
+
+
+@pytest.mark.parametrize("table", ["smrt", "shakhov"])
+def test_prandtl_two_thirds_from_decay_rates(lats, table):
+    """Sec. 3 / Table 4: tau_31 = tau_20 / Pr with Pr = 2/3, read off measured decay factors."""
+    lat = lats["D3Q39"]
+    star = S.TAU_STAR_SMRT if table == "smrt" else S.TAU_STAR_SHAKHOV
+    model = S.Model(lat, 3, tau_ref=1.7, tau_star=star, maxwell_law=False)
+    rng = np.random.default_rng(5)
+    rates = {}
+    for n, m in [(2, 0), (3, 1)]:
+        mode = H.components(_pure_mode(n, m, rng))
+        al = H.multi_indices_upto(3)
+        d = np.zeros((len(al), 1))
+        d[0, 0] = 1.0
+        k0 = [k for k, a in enumerate(al) if sum(a) == n and abs(mode[a]) > 1e-3][0]
+        for k, a in enumerate(al):
+            if sum(a) == n:
+                d[k, 0] = 1e-3 * mode[a]
+        f = S.rebuild(S.to_absolute(d, 3, np.zeros((3, 1)), np.ones(1)), lat, 3)
+        dh = S.local_direct(S.collide(f, model), lat, 3, np.zeros((3, 1)), np.ones(1))
+        lam = dh[k0, 0] / d[k0, 0]
+        rates[(n, m)] = 1.0 / (1.0 - lam) - 0.5       # continuous relaxation time
+    assert abs(rates[(2, 0)] / rates[(3, 1)] - 2.0 / 3.0) < 1e-12
+
+
+def test_bulk_mode_is_inert(lats):
+    """Sec. 4.2: tau_21 is absent for a monatomic gas -- changing it changes nothing."""
+    lat = lats["D3Q103"]
+    f, _ = _random_state(lat, 4, eps=0.3)
+    s1 = dict(S.TAU_STAR_SMRT)
+    s2 = dict(S.TAU_STAR_SMRT)
+    s2[(2, 1)] = 7.0
+    h1 = S.collide(f, S.Model(lat, 4, tau_ref=0.6, tau_star=s1))
+    h2 = S.collide(f, S.Model(lat, 4, tau_ref=0.6, tau_star=s2))
+    np.testing.assert_allclose(h1, h2, atol=1e-14)
+
+
+def test_periodic_uniform_equilibrium_invariant(lats):
+    lat = lats["D3Q39"]
+    model = S.Model(lat, 3, tau_ref=0.9)
+    geom = S.Geometry(shape=(3, 4, 5))
+    feq = S.equilibrium(np.array([1.2]), np.array([[0.1], [0.05], [-0.1]]), np.array([0.95]), lat, 3)
+    h = np.broadcast_to(feq[:, :, None, None], (lat.q, 3, 4, 5)).copy()
+    h2 = S.step(h, model, geom)
+    np.testing.assert_allclose(h2, h, atol=1e-14)
+
+
+def test_streaming_is_a_permutation(lats):
+    """Pull streaming by e_i + k moves populations without changing any value (periodic)."""
+    lat = lats["D3Q39"]
+    rng = np.random.default_rng(2)
+    h = rng.random((lat.q, 4, 5, 6))
+    geom = S.Geometry(shape=(4, 5, 6), shift=(1, 0, 0))
+    f = S.stream(h, lat, geom)
+    for i in range(lat.q):
+        assert np.allclose(np.sort(f[i].ravel()), np.sort(h[i].ravel()))
+        sx, sy, sz = lat.e[i] + np.array([1, 0, 0])
+        assert f[i][sz % 4, sy % 5, sx % 6] == h[i][0, 0, 0]

@@ -1,0 +1,84 @@
+"""Pins of the oracle's shock set-up (Eq. rankine, Table 3) and of a converged 1D shock."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import lattice as L
+from oracle import shock as K
+from oracle import smrt as S
+from _golden import rows
+
+
+def test_rankine_hugoniot_reproduces_table3():
+    """Each Table 3 row: rho2, theta2/theta1, (u1+u2)/2, k_x and u_bar_x from Ma and c_l."""
+    for r in rows("table3_implementation.txt"):
+        Ma, c_l = float(r[0]), float(r[3])
+        rho2, th1, th2, kx, ubar, mean = map(float, (r[4], r[5], r[6], r[7], r[8], r[9]))
+        st = K.rankine_hugoniot(Ma, theta1=th1)
+        assert abs(st["rho2"] - rho2) <= 0.005 + 1e-12
+        # theta1 and theta2 are printed to 2-3 significant digits: compare the ratio within that
+        ratio = th2 / th1
+        rel = 0.005 / th2 + 0.0005 / th1
+        assert abs(st["theta2"] / th1 - ratio) <= rel * ratio * 1.01
+        # the printed (u1+u2)/2 column is off by up to one unit in its last digit against the
+        # printed theta1 (Ma=5: 1.688 printed 1.68; Ma=7: 1.524 printed 1.53)
+        assert abs(K.mean_speed(Ma, th1) - mean) <= 0.01
+        assert abs(0.5 * (st["u1"] + st["u2"]) - K.mean_speed(Ma, th1)) < 1e-12
+        assert K.shift(Ma, th1, c_l) == int(kx)
+        assert abs(int(kx) * c_l - ubar) <= 0.005
+        # the jump half-width bounds the relative speed from below (Sec. 4.2)
+        assert abs(0.5 * (st["u1"] - st["u2"]) - K.half_jump(Ma, th1)) < 1e-12
+
+
+def test_first_power_misprint_would_not_reproduce_table3():
+    """The printed denominator (gamma+1)^2 Ma is a typo: it misses Table 3's Ma=3 theta ratio."""
+    g, Ma = K.GAMMA, 3.0
+    misprint = (2 * g * Ma ** 2 - g + 1) * ((g - 1) * Ma ** 2 + 2) / ((g + 1) ** 2 * Ma)
+    assert abs(misprint - 1.22 / 0.333) > 1.0
+    assert abs(K.rankine_hugoniot(Ma)["theta2"] - 1.22 / 0.333) < 0.03
+
+
+def test_theta_scale_keeps_hot_side_below_two():
+    for Ma in (1.2, 1.5, 3.0, 5.0, 7.0):
+        th1 = K.theta_scale(Ma)
+        assert K.rankine_hugoniot(Ma, theta1=th1)["theta2"] < 2.0
+
+
+@pytest.fixture(scope="module")
+def converged_shock():
+    """Ma = 1.2, D3Q39, N = 3, 400 cells, tanh width 10, ell = 2 cells, 2000 steps."""
+    lat = L.d3q39()
+    case = K.shock_case(lat, 3, 1.2, 400)
+    st = case.states
+    h = K.initial_state(case, synthetic.tanh_blend(400, 10, st["rho1"], st["rho2"]),
+                        synthetic.tanh_blend(400, 10, st["u1"], st["u2"]),
+                        synthetic.tanh_blend(400, 10, st["theta1"], st["theta2"]))
+    for _ in range(1900):
+        h = S.step(h, case.model, case.geom)
+    m_prev = S.macroscopic(h, case.model, case.geom)
+    for _ in range(100):
+        h = S.step(h, case.model, case.geom)
+    return case, S.macroscopic(h, case.model, case.geom), m_prev
+
+
+def test_converged_shock_is_steady_and_satisfies_rankine_hugoniot(converged_shock):
+    case, m, m_prev = converged_shock
+    st = case.states
+    assert case.k == 1 and abs(case.model.tau_ref - 2 * np.sqrt(1.5)) < 1e-12
+    # steady: density changes by < 1e-5 over the last 100 steps
+    assert np.abs(m["rho"] - m_prev["rho"]).max() < 1e-5
+    # far field equals the RH states
+    for key, i in (("rho", 10), ("theta", 10)):
+        assert abs(m[key][i] - st[key + "1"]) < 1e-5
+        assert abs(m[key][-10] - st[key + "2"]) < 1e-5
+    assert abs(m["u"][0][10] - st["u1"]) < 1e-5 and abs(m["u"][0][-10] - st["u2"]) < 1e-5
+    # mass flux rho u is uniform through the shock (discrete steady conservation)
+    flux = m["rho"] * m["u"][0]
+    assert np.abs(flux / (st["rho1"] * st["u1"]) - 1.0).max() < 1e-4
+    # the shock stays where it started
+    mid = 0.5 * (st["rho1"] + st["rho2"])
+    pos = np.argmin(np.abs(m["rho"] - mid))
+    assert abs(pos - 200) <= 2
+    # the profile is monotone and the heat flux inside the shock is negative (flows upstream)
+    assert np.all(np.diff(m["rho"]) > -1e-9)
+    assert m["q"][0][pos] < 0.0
