@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Throughput of the LB-SMRT fused collide-and-stream step on GB300.
+
+Workload (the HBM-roofline case): a 256^3 periodic box, D3Q39 velocity set, SMRT truncated at
+order N = 3 with the Maxwell-molecule relaxation times of Table 4, populations and arithmetic
+in FP32. Initial state: the order-3 equilibrium of rho = 1 + N(0, 1e-3^2) (seed 11086),
+theta = 1 and a Taylor-Green velocity field of amplitude 0.05 (synthetic.taylor_green), made on
+the device by lb_fill_equilibrium. One step = one launch of the fused kernel over all cells;
+the two 2.6 GB state buffers (5.2 GB) are far larger than the 129 MB L2, so every timed step
+streams from HBM.
+
+Metric: GLUPSxQ = cells x Q x steps / s (cell-velocity updates per second), with the fraction
+of the HBM roofline taken from the algorithmic traffic 2 Q 4 bytes per cell-step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (the plain CPU restatement of the method) on the host
+cores on a bounded sample of the same workload: the 32^3 corner block of the same Taylor-Green
+field stepped as its own periodic box. With N > 1 (torchrun), every rank runs its own box
+(replicas: the step has no exchange on one GPU) and value = all ranks' updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+Q = 39
+N_ORDER = 3
+METRIC = "GLUPSxQ (cell-velocity updates/s) and % HBM roofline"
+UNIT = "G cell-velocity updates/s"
+KERNEL_SOURCES = ["core.cuh", "kernels.cuh", "lattices.cuh", "dispatch.h"]
+PROFILE = os.path.join(ROOT, "profiles", "collide_stream_d3q39_f32_box.txt")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for n in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_11086_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(n: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to n^3 cells, or None
+    when the summary is missing or was taken on different kernel sources."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    with open(PROFILE) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha256_12") != kernel_hash():
+        return None
+    try:
+        per_cell = float(vals["dram_bytes_per_cell"])
+    except (KeyError, ValueError):
+        return None
+    return per_cell * n ** 3
+
+
+def tau_table():
+    # Table 4 (SMRT, Maxwell molecules) times tau_20; tau_20 from an upstream mean free path of
+    # 2 cells at theta = 1: tau_c = 2 c / sqrt(theta).
+    return [1.0, 1.0, 2.0 / 3.0, 1.5]
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for name, flag in zip(names, parts[5:9]):
+                    if flag.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rate(block: int, steps: int, warmup: int = 1) -> dict:
+    """FP64 oracle on the block^3 corner of the 256^3 Taylor-Green workload (own periodic box),
+    single-threaded BLAS; returns cell-velocity updates/s. Runs in a fresh spawned process."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import synthetic
+from oracle import lattice as L, smrt as S
+lat = L.d3q39()
+rho, u, th = synthetic.taylor_green(256)
+b = {block}
+rho, u, th = rho[:b, :b, :b], u[:, :b, :b, :b], th[:b, :b, :b]
+model = S.Model(lat, 3, tau_ref=2.0 * lat.c)
+geom = S.Geometry(shape=(b, b, b))
+h = S.equilibrium(rho.ravel(), u.reshape(3, -1), th.ravel(), lat, 3).reshape(lat.q, b, b, b)
+for _ in range({warmup}):
+    h = S.step(h, model, geom)
+t0 = time.perf_counter()
+for _ in range({steps}):
+    h = S.step(h, model, geom)
+dt = time.perf_counter() - t0
+print(json.dumps({{"rate": b ** 3 * lat.q * {steps} / dt, "seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle baseline failed: {res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    # size the sampled block so that warm-up + timed steps stay near 90 s of oracle work
+    # (about 24 us per cell-step for the FP64 oracle on one core)
+    budget_cells = 90.0 / max(1, args.steps + args.warmup) / 24e-6
+    block = int(max(8, min(32, round(budget_cells ** (1.0 / 3.0)))))
+    t0 = time.perf_counter()
+    r = oracle_sample_rate(block, args.steps, args.warmup)
+    wall = time.perf_counter() - t0
+    value = r["rate"] / 1e9
+    sample = f"{block}^3 corner block of the 256^3 Taylor-Green box, {args.steps} oracle steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * r["seconds"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "box256_d3q39_n3_f32", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2401_11086_gb300 as P
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    n = args.n
+    d = P.lb_lattice_named("D3Q39")
+    stream = torch.cuda.current_stream()
+    ctx = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree), n, n, n, N=N_ORDER,
+                            precision="f32", stream=stream)
+    tau20 = 2.0 * d.c
+    P.lb_set_relaxation(ctx, [r * tau20 for r in tau_table()], True, 1.0)
+    rho, u, th = synthetic.taylor_green(n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    fa, fb = ctx.new_state(), ctx.new_state()
+    P.lb_fill_equilibrium(ctx, fa, dev(rho.ravel()), dev(u.reshape(3, -1)), dev(th.ravel()))
+    del rho, u, th
+    torch.cuda.synchronize()
+
+    cur, other = fa, fb
+    for _ in range(args.warmup):
+        cur = P.lb_step(ctx, cur, other, 1)
+        other = fa if cur is fb else fb
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        cur = P.lb_step(ctx, cur, other, 1)
+        ev[k][1].record(stream)
+        other = fa if cur is fb else fb
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    st, flags = P.lb_poll_status(ctx)
+    if st != 0:
+        raise SystemExit(f"health word reports status {st} (flags {flags})")
+
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    cells = n ** 3
+    value = world * cells * Q * K / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: every step copies the state in from
+    # pinned host memory, steps once, and copies the new state back
+    state_bytes = ctx.state_elems * 4
+    host_in = torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True)
+    host_out = torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True)
+    host_in.copy_(cur)
+    E = args.e2e_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(E):
+        fa.copy_(host_in, non_blocking=True)
+        res = P.lb_step(ctx, fa, fb, 1)
+        host_out.copy_(res, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / E
+    e2e_value = world * cells * Q / (e2e_ms * 1e-3) / 1e9
+
+    peak, peak_kind = measured_peak()
+    alg_bytes = 2.0 * Q * 4 * cells
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    traffic = profile_traffic(n)
+
+    if rank != 0:
+        ctx.close()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_sample_rate(32, 20)
+        cpu = {"value": r["rate"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "32^3 corner block of the 256^3 Taylor-Green box stepped as its own "
+                         "periodic box, 20 FP64 oracle steps, single-threaded BLAS"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "box256_d3q39_n3_f32", "cells": cells, "velocities": Q,
+                   "hermite_order": N_ORDER, "init": "Taylor-Green A=0.05, rho noise 1e-3",
+                   "l2": "inputs larger than L2 (two 2.6 GB state buffers)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": kern_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": K,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

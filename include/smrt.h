@@ -1,0 +1,192 @@
+/*
+ * smrt.h -- C ABI of libsmrt, the GB300 (sm_103a) implementation of the LB-SMRT
+ * collide-and-stream step of Yan & Shan, "Lattice Boltzmann simulation of non-equilibrium
+ * flows using spectral multiple-relaxation-time collision model" (arXiv 2401.11086).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units.   Lattice units: one time step, cell size c. Population i has the lattice abscissa
+ *          xi_i = c e_i (e_i an integer vector) relative to the frame velocity u_bar = c k,
+ *          k = lattice->shift (Sec. 4.1, "shifted stencil"); its physical velocity is
+ *          xi_i + u_bar and it streams by e_i + k cells per step. Velocities passed in or out
+ *          of the library (lb_state.u, lb_fill_equilibrium's u, lb_moments' u) are PHYSICAL
+ *          (they include u_bar); theta is the temperature in units of the reference
+ *          temperature ("energy units", Sec. 2).
+ * State.   A state is the set of post-collision populations of every cell, structure of
+ *          arrays: element  f[i * plane_stride + cell]  for population i (the caller's
+ *          lattice order) and cell = instance_offset + (z * ny + y) * nx + x, x fastest.
+ *          Instances (batched 1D problems) are concatenated in order. plane_stride and the
+ *          element count of a state are given by lb_plane_stride / lb_state_elems.
+ *          The element type is double for LB_F64 and float otherwise.
+ * Memory.  Every pointer argument named f*, out, rho, u, theta, lam*, dtau is DEVICE memory
+ *          owned by the caller. The library owns only the context and its small device tables.
+ *          lb_step, lb_moments and lb_fill_equilibrium allocate nothing.
+ * Streams. All device work of a context is enqueued on the stream given to lb_init_lattice
+ *          (a cudaStream_t passed as void*, NULL = legacy default stream) and is asynchronous;
+ *          only lb_poll_status synchronises. One context per stream; calls on one context are
+ *          not thread-safe.
+ * Errors.  Arguments are validated before any launch (LB_ERR_INVALID, nothing enqueued).
+ *          Device-side trouble is recorded in a health word read by lb_poll_status. No C++
+ *          exception crosses this ABI.
+ */
+#ifndef SMRT_H
+#define SMRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx; /* opaque; created by lb_init_lattice, freed by lb_destroy */
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = 1,     /* bad pointer, size, lattice or parameter; nothing was enqueued */
+    LB_ERR_CUDA = 2,        /* a CUDA runtime call failed                                     */
+    LB_ERR_UNSTABLE = 3,    /* a cell reached rho <= 0, theta <= 0 or NaN (health word)       */
+    LB_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (health word)               */
+    LB_ERR_UNSUPPORTED = 5, /* valid request this build has no kernel for                     */
+    LB_ERR_NOMEM = 6        /* allocation of the context's own tables failed                  */
+} lb_status;
+
+typedef enum {
+    LB_F64 = 0,        /* populations and all arithmetic in double                           */
+    LB_F32 = 1,        /* populations and all arithmetic in float                            */
+    LB_F32_CONS64 = 2  /* float populations; the conserved sums (rho, rho u, energy) and the
+                          equilibrium part of the rebuild in double                          */
+} lb_precision;
+
+/* Health-word bits returned by lb_poll_status. */
+#define LB_HEALTH_UNSTABLE 0x1u /* some cell had rho <= 0, theta <= 0 or a NaN moment */
+#define LB_HEALTH_TIMEOUT 0x2u
+
+/* Velocity set: a degree-`degree` Gauss-Hermite quadrature (Sec. 3, Eq. an): abscissae
+ * xi_i = c e_i, weights w_i. e is q*3 int8 (row i = e_i), w is q doubles; both host memory,
+ * copied by lb_init_lattice. shift = k, the integer frame shift of Sec. 4.1. */
+typedef struct {
+    int q;
+    const int8_t *e;
+    const double *w;
+    double c;
+    int degree;
+    int shift[3];
+} lb_lattice_desc;
+
+/* Grid. Single instance: nx, ny, nz cells, batch = 1, nx_per_instance = NULL.
+ * Batched 1D problems: ny = nz = 1, batch = B, nx_per_instance = B lengths (host memory,
+ * copied), nx ignored. bc_x: 0 periodic in x, 1 fixed end states in x (cells beyond either
+ * end hold the order-N equilibrium of the left/right state; Sec. 4.2). y and z are periodic. */
+typedef struct {
+    int nx, ny, nz;
+    int batch;
+    const int *nx_per_instance;
+    int bc_x;
+} lb_grid_desc;
+
+/* A macroscopic state: density, PHYSICAL velocity, temperature (Sec. 2, Eq. Maxwellian). */
+typedef struct {
+    double rho, u[3], theta;
+} lb_state;
+
+/* lb_init_lattice -- create a context for one velocity set, grid, truncation order and
+ * precision. The velocity set must integrate every monomial of degree <= 2N exactly (Sec. 3,
+ * the exactness remark after Eq. fi); the library checks this by brute force and also
+ * matches e against the velocity sets it has kernels for (LB_ERR_UNSUPPORTED otherwise).
+ * hermite_order N: truncation order of Eqs. an/fi (2 <= N <= 4 in this build).
+ * cuda_stream: cudaStream_t used for every later call on this context.
+ * On success *out is a new context (relaxation times unset: lb_set_relaxation must follow).
+ * Errors: LB_ERR_INVALID (null/size/quadrature), LB_ERR_UNSUPPORTED, LB_ERR_NOMEM, LB_ERR_CUDA. */
+lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lattice, const lb_grid_desc *grid,
+                          int hermite_order, lb_precision precision, void *cuda_stream);
+
+/* lb_set_relaxation -- relaxation times of the SMRT operator (Eq. SMRT) and end states.
+ * tau: continuous relaxation times tau_c,nm in time steps at density rho_ref, one per
+ *      irreducible part (n, m), n = 2..N, m = 0..floor(n/2), in the order
+ *      (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2) (host memory; 2 entries for N=2, 4 for N=3, 7 for N=4). Table 4 gives tau_nm / tau_20 for Maxwell molecules.
+ *      The discrete time of part (n,m) at a cell is tau_c,nm * s + 1/2, with s = rho_ref/rho
+ *      when maxwell_molecule_law is 1 (viscosity proportional to temperature, Sec. 4.2) and
+ *      s = 1 when it is 0. Every tau must be > 0.
+ * left, right: end states of a grid with bc_x = 1 (host memory; may be NULL when bc_x = 0).
+ * instance: which instance of a batch to set (-1 = all).
+ * Enqueues the computation of the end-state populations on the context's stream.
+ * Errors: LB_ERR_INVALID (null, tau <= 0, rho or theta <= 0, bad instance), LB_ERR_CUDA. */
+lb_status lb_set_relaxation(lb_ctx *ctx, const double *tau, int maxwell_molecule_law,
+                            double rho_ref, const lb_state *left, const lb_state *right,
+                            int instance);
+
+/* lb_set_frame_shift -- change the integer frame shift k_x of one instance (-1 = all) after
+ * lb_init_lattice (Sec. 4.1: each shock chooses k_x = round(((u1 + u2)/2) / c)). Call before
+ * lb_set_relaxation so that the end-state populations use the new frame. Synchronises.
+ * Errors: LB_ERR_INVALID (bad instance; a single box accepts only -1), LB_ERR_CUDA. */
+lb_status lb_set_frame_shift(lb_ctx *ctx, int instance, int kx);
+
+/* lb_fill_equilibrium -- f = order-N truncated Maxwellian of the given fields at every cell
+ * (Sec. 3: f_i^eq is the truncated Hermite expansion of Eq. Maxwellian evaluated at xi_i,
+ * built through Eq. fi). rho, theta: ncells doubles; u: 3*ncells doubles (row k = component
+ * k of the PHYSICAL velocity), all device memory; f: a state (device). This is the
+ * post-collision state of an equilibrium, i.e. a valid initial state.
+ * Errors: LB_ERR_INVALID, LB_ERR_CUDA. */
+lb_status lb_fill_equilibrium(lb_ctx *ctx, void *f, const double *rho, const double *u,
+                              const double *theta);
+
+/* lb_step -- advance nsteps collide-and-stream steps (Sec. 3: stream f_i along e_i + k, then
+ * the SMRT collision of Eq. SMRT through the irreducible decomposition of Appendix A and the
+ * rebuild of Eq. fi). The state enters in f_a. Steps alternate f_a -> f_b -> f_a ...; after
+ * the call the newest state is in f_b when nsteps is odd and in f_a when nsteps is even
+ * (for nsteps = 1, f_a is read only). f_a and f_b must be distinct, non-overlapping states.
+ * Errors: LB_ERR_INVALID (null, nsteps < 1, relaxation unset), LB_ERR_CUDA. */
+lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
+
+/* Row groups of lb_moments' output, selected by which_mask. */
+#define LB_MOM_RHO 0x1u   /* 1 row:  rho                                                    */
+#define LB_MOM_U 0x2u     /* 3 rows: physical velocity u_x, u_y, u_z                        */
+#define LB_MOM_THETA 0x4u /* 1 row:  theta                                                  */
+#define LB_MOM_SIGMA 0x8u /* 6 rows: sigma = theta d^(2): xx yy zz xy xz yz                 */
+#define LB_MOM_Q 0x10u    /* 3 rows: heat flux q_k = theta^(3/2)/2 sum_l d^(3)_kll          */
+#define LB_MOM_D 0x20u    /* M rows: local coefficients d_beta, |beta| <= max(N,3)          */
+
+/* lb_moments -- macroscopic moments of the PRE-collision populations (the state streamed by
+ * one step, without colliding) at every cell: rho, u, theta (Sec. 2, Eq. hermite), and the
+ * local-frame Hermite coefficients d_beta = sum_i f_i He_beta((xi_i - u)/sqrt(theta)) of the
+ * expansion that defines SMRT (Sec. 3), with sigma and q derived from them (Sec. 2.2:
+ * a^(2) = P/p - delta, q_i = Q_ikk/2). Multi-indices beta are ordered by order, then
+ * descending lexicographically ((2,0,0) (1,1,0) (1,0,1) (0,2,0) (0,1,1) (0,0,2) ...).
+ * out: device doubles, rows of lb_cells(ctx) values, the selected groups in the order of
+ * the bits above. Errors: LB_ERR_INVALID, LB_ERR_CUDA. */
+lb_status lb_moments(lb_ctx *ctx, const void *f, double *out, unsigned which_mask);
+
+/* lb_poll_status -- synchronise the context's stream, return and clear its health word.
+ * Returns LB_ERR_UNSTABLE / LB_ERR_TIMEOUT when the corresponding bit was set, LB_ERR_CUDA
+ * when the stream reports an error, LB_OK otherwise. health_flags may be NULL. */
+lb_status lb_poll_status(lb_ctx *ctx, unsigned *health_flags);
+
+/* Sizes of a context's arrays. */
+size_t lb_cells(const lb_ctx *ctx);       /* total cells over all instances              */
+size_t lb_plane_stride(const lb_ctx *ctx); /* elements between population planes          */
+size_t lb_state_elems(const lb_ctx *ctx);  /* elements of one state = q * plane_stride    */
+int lb_num_moment_rows(const lb_ctx *ctx, unsigned which_mask);
+
+/* lb_lattice_named -- the library's own velocity sets, solved from the even-moment
+ * conditions of a degree-Q Gauss-Hermite rule (Sec. 3, Eq. an): "D3Q39" (degree 7) and
+ * "D3Q103" (degree 9). Writes up to capacity velocities: e_out (capacity*3 int8), w_out
+ * (capacity doubles), *c_out, *q_out, *degree_out (host memory).
+ * Errors: LB_ERR_INVALID (unknown name, null, capacity too small). */
+lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w_out, double *c_out,
+                           int *q_out, int *degree_out, int capacity);
+
+/* lb_rankine_hugoniot -- end states of a normal shock (Eq. rankine, temperature ratio read
+ * with Ma^2 in the denominator) for upstream Mach number Ma, ratio of specific heats gamma,
+ * upstream rho1 and theta1; velocities in the shock frame, along +x (host memory out). */
+lb_status lb_rankine_hugoniot(double Ma, double gamma, double rho1, double theta1,
+                              lb_state *left, lb_state *right);
+
+const char *lb_error_string(lb_status status);
+void lb_destroy(lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMRT_H */

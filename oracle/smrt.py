@@ -242,6 +242,24 @@ def stream(h, lat: Lattice, geom: Geometry):
     return out
 
 
+def pull_cells(h, lat: Lattice, geom: Geometry, cells):
+    """Pre-collision populations (Q, len(cells)) at the listed flat cell indices of a periodic
+    field h (Q, nz, ny, nx): f_i(x) = h_i(x - e_i - k), each axis wrapped. The same rule as
+    ``stream``, evaluated only where asked."""
+    nz, ny, nx = geom.shape
+    cells = np.asarray(cells)
+    z, rem = np.divmod(cells, ny * nx)
+    y, x = np.divmod(rem, nx)
+    kx, ky, kz = geom.shift
+    out = np.empty((lat.q, len(cells)), dtype=h.dtype)
+    for i in range(lat.q):
+        xs = (x - lat.e[i, 0] - kx) % nx
+        ys = (y - lat.e[i, 1] - ky) % ny
+        zs = (z - lat.e[i, 2] - kz) % nz
+        out[i] = h[i][zs, ys, xs]
+    return out
+
+
 def collide_field(f, model: Model, chunk: int = 4096):
     """Collide every cell of a (Q, nz, ny, nx) field, in chunks of cells."""
     Q = f.shape[0]

@@ -1,0 +1,135 @@
+// dispatch.h -- what the C-ABI layer (api.cu) needs to launch the templated kernels that the
+// per-lattice, per-precision translation units instantiate.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace smrt {
+
+constexpr int kMaxQ = 103;
+constexpr int kMaxNP = 51;
+constexpr int kTile = 128;  // cells per block (threads per block) for every kernel
+
+// Everything a launch needs, in library population order.
+struct CtxView {
+    cudaStream_t stream;
+    long long plane[kMaxQ];
+    double wp[kMaxNP + 1];
+    double c;
+    int nx, ny, nz;
+    int kx, ky, kz;
+    int line;    // 1: batched 1D lines (tiles), 0: periodic box
+    int fixedx;  // line mode: fixed end states in x
+    const InstanceInfo *inst;
+    const int2 *tiles;
+    int ntiles;
+    const void *ghosts;
+    unsigned *health;
+    long long ncells;
+};
+
+using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
+using MomentsFn = cudaError_t (*)(const CtxView &, const void *f, double *out, unsigned mask);
+using FillFn = cudaError_t (*)(const CtxView &, void *f, const double *rho, const double *u,
+                               const double *theta);
+using GhostFn = cudaError_t (*)(const CtxView &, const double *states, int ninst, void *ghosts);
+
+struct KernelSet {
+    StepFn step;
+    MomentsFn moments;
+    FillFn fill;
+    GhostFn ghost;
+};
+
+// precision: 0 double, 1 float, 2 float with double conserved sums and equilibrium rebuild
+const KernelSet *kernels_d3q39(int N, int precision);
+const KernelSet *kernels_d3q103(int N, int precision);
+
+template <class Lat, class T>
+StepArgs<Lat, T> make_args(const CtxView &v, const void *fin, void *fout) {
+    StepArgs<Lat, T> a;
+    a.fin = static_cast<const T *>(fin);
+    a.fout = static_cast<T *>(fout);
+    a.inst = v.inst;
+    a.tiles = v.tiles;
+    a.ghosts = static_cast<const T *>(v.ghosts);
+    a.health = v.health;
+    for (int i = 0; i < Lat::Q; ++i) a.plane[i] = v.plane[i];
+    for (int p = 0; p <= Lat::NP; ++p) a.wp[p] = T(v.wp[p]);
+    a.c = T(v.c);
+    a.nx = v.nx;
+    a.ny = v.ny;
+    a.nz = v.nz;
+    a.kx = v.kx;
+    a.ky = v.ky;
+    a.kz = v.kz;
+    return a;
+}
+
+template <class Lat, int N, class T, class Acc, bool Split>
+cudaError_t launch_step(const CtxView &v, const void *fin, void *fout) {
+    const StepArgs<Lat, T> a = make_args<Lat, T>(v, fin, fout);
+    if (v.line) {
+        if (v.fixedx)
+            step_line_kernel<Lat, N, T, Acc, Split, true><<<v.ntiles, kTile, 0, v.stream>>>(a);
+        else
+            step_line_kernel<Lat, N, T, Acc, Split, false><<<v.ntiles, kTile, 0, v.stream>>>(a);
+    } else {
+        const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
+        step_box_kernel<Lat, N, T, Acc, Split><<<grid, kTile, 0, v.stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, class T, class Acc>
+cudaError_t launch_moments(const CtxView &v, const void *f, double *out, unsigned mask) {
+    MomentArgs<Lat, N, T, Acc> m;
+    m.s = make_args<Lat, T>(v, f, nullptr);
+    m.out = out;
+    m.ncells = v.ncells;
+    m.mask = mask;
+    m.line = v.line;
+    m.fixedx = v.fixedx;
+    if (v.line) {
+        moments_kernel<Lat, N, T, Acc><<<v.ntiles, kTile, 0, v.stream>>>(m);
+    } else {
+        const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
+        moments_kernel<Lat, N, T, Acc><<<grid, kTile, 0, v.stream>>>(m);
+    }
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, class T>
+cudaError_t launch_fill(const CtxView &v, void *f, const double *rho, const double *u,
+                        const double *theta) {
+    const StepArgs<Lat, T> a = make_args<Lat, T>(v, nullptr, f);
+    if (v.line) {
+        fill_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(a, rho, u, theta, v.ncells, 1);
+    } else {
+        const long long nb = (v.ncells + kTile - 1) / kTile;
+        fill_kernel<Lat, N, T><<<(unsigned)nb, kTile, 0, v.stream>>>(a, rho, u, theta, v.ncells, 0);
+    }
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, class T>
+cudaError_t launch_ghost(const CtxView &v, const double *states, int ninst, void *ghosts) {
+    const StepArgs<Lat, T> a = make_args<Lat, T>(v, nullptr, nullptr);
+    const int n = 2 * ninst;
+    ghost_kernel<Lat, N, T><<<(n + 63) / 64, 64, 0, v.stream>>>(a, states, ninst, static_cast<T *>(ghosts));
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, int P>
+const KernelSet *kernel_set() {
+    using T = typename std::conditional<P == 0, double, float>::type;
+    using Acc = typename std::conditional<P == 1, float, double>::type;
+    constexpr bool Split = (P == 2);
+    static const KernelSet ks = {&launch_step<Lat, N, T, Acc, Split>, &launch_moments<Lat, N, T, Acc>,
+                                 &launch_fill<Lat, N, T>, &launch_ghost<Lat, N, T>};
+    return &ks;
+}
+
+}  // namespace smrt

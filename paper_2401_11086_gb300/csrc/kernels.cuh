@@ -1,0 +1,517 @@
+// kernels.cuh -- the fused collide-and-stream kernel of LB-SMRT and its helpers
+// (Yan & Shan, arXiv 2401.11086), templated on the velocity set, the truncation order N,
+// the storage/arithmetic type T and the type Acc of the conserved sums.
+//
+// Per cell and step (one thread per cell, pull scheme, structure-of-arrays populations):
+//   a1  pull f_i from x - e_i - k of the previous state (Sec. 3 streaming with the shifted
+//       stencil of Sec. 4.1); cells beyond a fixed x end read the end state's equilibrium
+//       (Sec. 4.2);
+//   a2  conserved sums rho, rho u, rho(|u|^2 + 3 theta) in Acc (Eq. hermite1 moments);
+//   a3  raw lattice moments R_gamma = sum_i f_i e_i^gamma, |gamma| <= N, with +-e pairs folded,
+//       then the absolute Hermite coefficients a_alpha = sum_i f_i He_alpha(xi_i) (Eq. an);
+//   a4  binomial transform to the local frame, d = T(u, theta)^-1 a (Sec. 3);
+//   a5  irreducible split and relaxation of each order n >= 2 with its own times (Eq. SMRT,
+//       Appendix A), orders 0 and 1 untouched;
+//   a6  back to the absolute frame, truncated at N;
+//   a7  rebuild f_i' = w_i sum_alpha a'_alpha He_alpha(xi_i)/alpha! (Eq. fi) as a polynomial in
+//       the integer e_i, evaluated once per +-e pair (even and odd parts);
+//   a8  store f_i' at x (aligned, coalesced).
+// Relaxation times: 1/tau_nm(x) = rho / (A_nm + B_nm rho), which covers both the
+// Maxwell-molecule law tau_nm = tau_c,nm rho_ref / rho + 1/2 (A = tau_c rho_ref, B = 1/2) and
+// constant times (A = 0, B = tau_c + 1/2).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "core.cuh"
+#include "lattices.cuh"
+
+namespace smrt {
+
+constexpr int kMaxTau = 10;
+
+struct InstanceInfo {
+    long long cell_off;  // first cell of the instance in the concatenated cell index
+    int nx;              // cells along x
+    int kx;              // frame shift along x (u_bar_x = c kx)
+    double tauA[kMaxTau];
+    double tauB[kMaxTau];
+};
+
+template <class Lat, class T>
+struct StepArgs {
+    const T *__restrict__ fin;
+    T *__restrict__ fout;
+    const InstanceInfo *__restrict__ inst;
+    const int2 *__restrict__ tiles;  // line kernel: (instance, first x) per block
+    const T *__restrict__ ghosts;    // [instance][2][Q], library order
+    unsigned *health;
+    long long plane[Lat::Q];  // element offset of each population plane, library order
+    T wp[Lat::NP + 1];        // weight of the rest velocity, then of each pair
+    T c;
+    int nx, ny, nz;           // box kernel geometry
+    int kx, ky, kz;           // box kernel frame shift
+};
+
+template <class T>
+SMRT_HD T rcp_tau(double A, double B, T rho) {
+    return rho / (T(A) + T(B) * rho);
+}
+
+// ------------------------------------------------------------------------------ collision
+template <class Lat, int N, class T, class Acc, bool Split>
+struct Collide {
+    static constexpr int Q = Lat::Q;
+    static constexpr int NP = Lat::NP;
+    static constexpr int M = nmom(N);
+    static constexpr int KT = ntau(N);
+
+    // a2: conserved sums, in Acc.
+    SMRT_HD static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc (&u)[3], Acc &theta) {
+        Acc r = Acc(f[0]), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
+        static_for<NP>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
+            constexpr int ee = e0 * e0 + e1 * e1 + e2 * e2;
+            const Acc sp = Acc(f[2 * p + 1]) + Acc(f[2 * p + 2]);
+            const Acc dp = Acc(f[2 * p + 1]) - Acc(f[2 * p + 2]);
+            r += sp;
+            if constexpr (e0 != 0) j0 = fma(Acc(e0), dp, j0);
+            if constexpr (e1 != 0) j1 = fma(Acc(e1), dp, j1);
+            if constexpr (e2 != 0) j2 = fma(Acc(e2), dp, j2);
+            en = fma(Acc(ee), sp, en);
+        });
+        rho = r;
+        const Acc ir = Acc(1) / r;
+        u[0] = c * j0 * ir;
+        u[1] = c * j1 * ir;
+        u[2] = c * j2 * ir;
+        theta = (c * c * en * ir - (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) * Acc(1.0 / 3.0);
+    }
+
+    // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma,
+    // R_gamma = sum_i f_i e_i^gamma, pairs folded: even |gamma| use f+ + f-, odd use f+ - f-.
+    template <int Nm>
+    SMRT_HD static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)]) {
+        constexpr int Mm = nmom(Nm);
+        T S[NP], D[NP];
+        static_for<NP>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            S[p] = f[2 * p + 1] + f[2 * p + 2];
+            D[p] = f[2 * p + 1] - f[2 * p + 2];
+        });
+        T cp[Nm + 1];
+        cp[0] = T(1);
+        static_for<Nm>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
+        T Rc[Mm];
+        static_for<Mm>([&](auto G) {
+            constexpr int g = decltype(G)::value;
+            constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+            constexpr bool even = ((g0 + g1 + g2) & 1) == 0;
+            T acc = (g == 0) ? f[0] : T(0);
+            static_for<NP>([&](auto P) {
+                constexpr int p = decltype(P)::value;
+                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                if constexpr (m != 0) {
+                    if constexpr (even)
+                        acc = fma(T(m), S[p], acc);
+                    else
+                        acc = fma(T(m), D[p], acc);
+                }
+            });
+            Rc[g] = acc * cp[g0 + g1 + g2];
+        });
+        static_for<Mm>([&](auto A) {
+            constexpr int al = decltype(A)::value;
+            T acc = T(0);
+            static_for<Mm>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr double h = hdiv(al, g);
+                if constexpr (h != 0.0) acc = fma(T(h), Rc[g], acc);
+            });
+            ta[al] = acc;
+        });
+    }
+
+    // a4: td_beta = d_beta / beta! = theta^(-|beta|/2) [T(-u, 2 - theta) ta]_beta
+    template <int Nm>
+    SMRT_HD static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta) {
+        T G[3][Nm + 1];
+        static_for<3>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            maxwell_divided<Nm, T>(G[k], -u[k], T(1) - theta);
+        });
+        binomial_divided<Nm, T>(v, G);
+        const T is = T(1) / sqrt(theta);
+        T sp[Nm + 1];
+        sp[0] = T(1);
+        static_for<Nm>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * is; });
+        static_for<nmom(Nm)>([&](auto A) {
+            constexpr int p = decltype(A)::value;
+            if constexpr (mi_order(p) >= 1) v[p] *= sp[mi_order(p)];
+        });
+    }
+
+    // a7 + a8 helper: values f'_i = w_i sum_gamma P_gamma e_i^gamma with
+    // P_gamma = c^|gamma| sum_alpha hfull(alpha, gamma) ta'_alpha; U is the arithmetic type.
+    template <class U>
+    SMRT_HD static void rebuild(const U (&ta)[M], U c, const T (&wp)[NP + 1], U (&out)[Q]) {
+        U cp[N + 1];
+        cp[0] = U(1);
+        static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
+        U P[M];
+        static_for<M>([&](auto G) {
+            constexpr int g = decltype(G)::value;
+            U acc = U(0);
+            static_for<M>([&](auto A) {
+                constexpr int al = decltype(A)::value;
+                constexpr double h = hfull(al, g);
+                if constexpr (h != 0.0) acc = fma(U(h), ta[al], acc);
+            });
+            P[g] = acc * cp[mi_order(g)];
+        });
+        out[0] = U(wp[0]) * P[0];
+        static_for<NP>([&](auto Pp) {
+            constexpr int p = decltype(Pp)::value;
+            U ev = U(0), od = U(0);
+            static_for<M>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                if constexpr (m != 0) {
+                    if constexpr (((g0 + g1 + g2) & 1) == 0)
+                        ev = fma(U(m), P[g], ev);
+                    else
+                        od = fma(U(m), P[g], od);
+                }
+            });
+            const U w = U(wp[p + 1]);
+            out[2 * p + 1] = w * (ev + od);
+            out[2 * p + 2] = w * (ev - od);
+        });
+    }
+
+    // ta^eq_alpha = rho prod_k g_{alpha_k}(u_k, theta) / alpha_k!  (3D product of the
+    // Appendix B closed form), computed in U.
+    template <class U>
+    SMRT_HD static void equilibrium(U rho, const U (&u)[3], U theta, U (&ta)[M]) {
+        U G[3][N + 1];
+        static_for<3>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            maxwell_divided<N, U>(G[k], u[k], theta - U(1));
+        });
+        static_for<M>([&](auto A) {
+            constexpr int p = decltype(A)::value;
+            ta[p] = rho * G[0][mi_comp(p, 0)] * G[1][mi_comp(p, 1)] * G[2][mi_comp(p, 2)];
+        });
+    }
+
+    // The whole collision: f (pre-collision, library order) -> f (post-collision).
+    // Returns false when rho or theta is not positive (or NaN).
+    SMRT_HD static bool collide(T (&f)[Q], const T (&wp)[NP + 1], T c, const double *tauA,
+                                const double *tauB) {
+        Acc rho_a, u_a[3], th_a;
+        conserved(f, Acc(c), rho_a, u_a, th_a);
+        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
+        const T rho = T(rho_a), theta = T(th_a);
+        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
+
+        T v[M];
+        absolute<N>(f, c, v);
+        to_local<N>(v, u, theta);
+
+        // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u
+        T s[KT];
+        static_for<KT>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
+        });
+        static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
+
+        // a6: back to the absolute frame: scale by theta^(|beta|/2), transform with T(u, theta)
+        const T sq = sqrt(theta);
+        T sp[N + 1];
+        sp[0] = T(1);
+        static_for<N>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * sq; });
+        static_for<M>([&](auto A) {
+            constexpr int p = decltype(A)::value;
+            if constexpr (mi_order(p) == 0)
+                v[p] = Split ? T(0) : rho;
+            else if constexpr (mi_order(p) == 1)
+                v[p] = T(0);
+            else
+                v[p] *= sp[mi_order(p)];
+        });
+        T G[3][N + 1];
+        static_for<3>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            maxwell_divided<N, T>(G[k], u[k], theta - T(1));
+        });
+        binomial_divided<N, T>(v, G);
+
+        if constexpr (!Split) {
+            T out[Q];
+            rebuild<T>(v, c, wp, out);
+            static_for<Q>([&](auto I) { f[decltype(I)::value] = out[decltype(I)::value]; });
+        } else {
+            // equilibrium part in Acc from the Acc moments, non-equilibrium part in T
+            Acc teq[M];
+            equilibrium<Acc>(rho_a, u_a, th_a, teq);
+            Acc oeq[Q];
+            rebuild<Acc>(teq, Acc(c), wp, oeq);
+            T oneq[Q];
+            rebuild<T>(v, c, wp, oneq);
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = T(oeq[i] + Acc(oneq[i]));
+            });
+        }
+        return ok;
+    }
+};
+
+// ------------------------------------------------------------------------------ loaders
+SMRT_HD int wrap(int t, int n) { return t < 0 ? t + n : (t >= n ? t - n : t); }
+
+// Periodic 3D box: one thread per cell, block covers a run of x, grid (x-blocks, ny, nz).
+template <class Lat, int N, class T, class Acc, bool Split>
+__global__ void __launch_bounds__(128) step_box_kernel(StepArgs<Lat, T> a) {
+    using C = Collide<Lat, N, T, Acc, Split>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= a.nx) return;
+    const long long row = (long long)a.nx;
+    const long long slab = row * a.ny;
+    T f[Lat::Q];
+    f[0] = a.fin[a.plane[0] + z * slab + y * row + x];
+    static_for<Lat::NP>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        static_for<2>([&](auto Sg) {
+            constexpr int sg = decltype(Sg)::value == 0 ? 1 : -1;
+            constexpr int i = 2 * p + 1 + decltype(Sg)::value;
+            const int xs = wrap(x - (sg * Lat::e(p, 0) + a.kx), a.nx);
+            const int ys = wrap(y - (sg * Lat::e(p, 1) + a.ky), a.ny);
+            const int zs = wrap(z - (sg * Lat::e(p, 2) + a.kz), a.nz);
+            f[i] = a.fin[a.plane[i] + zs * slab + ys * row + xs];
+        });
+    });
+    const bool ok = C::collide(f, a.wp, a.c, a.inst[0].tauA, a.inst[0].tauB);
+    if (!ok) atomicOr(a.health, 1u);
+    const long long cell = z * slab + y * row + x;
+    static_for<Lat::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        a.fout[a.plane[i] + cell] = f[i];
+    });
+}
+
+// Batched 1D lines (ny = nz = 1): block b handles cells x0 .. x0+blockDim-1 of instance j,
+// (j, x0) = tiles[b]. FixedX: pulls from beyond either end read the end-state populations.
+template <class Lat, int N, class T, class Acc, bool Split, bool FixedX>
+__global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
+    using C = Collide<Lat, N, T, Acc, Split>;
+    const int2 tile = a.tiles[blockIdx.x];
+    const InstanceInfo &in = a.inst[tile.x];
+    const int x = tile.y + threadIdx.x;
+    const int L = in.nx;
+    if (x >= L) return;
+    const long long base = in.cell_off;
+    const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
+    const T *gr = gl + Lat::Q;
+    T f[Lat::Q];
+    f[0] = a.fin[a.plane[0] + base + x];
+    static_for<Lat::NP>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        static_for<2>([&](auto Sg) {
+            constexpr int sg = decltype(Sg)::value == 0 ? 1 : -1;
+            constexpr int i = 2 * p + 1 + decltype(Sg)::value;
+            const int xs = x - (sg * Lat::e(p, 0) + in.kx);
+            if constexpr (FixedX) {
+                if (xs < 0)
+                    f[i] = gl[i];
+                else if (xs >= L)
+                    f[i] = gr[i];
+                else
+                    f[i] = a.fin[a.plane[i] + base + xs];
+            } else {
+                f[i] = a.fin[a.plane[i] + base + wrap(xs, L)];
+            }
+        });
+    });
+    const bool ok = C::collide(f, a.wp, a.c, in.tauA, in.tauB);
+    if (!ok) atomicOr(a.health, 1u);
+    static_for<Lat::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        a.fout[a.plane[i] + base + x] = f[i];
+    });
+}
+
+// ------------------------------------------------------------------------------ moments
+// Moments of the pulled (pre-collision) populations; see lb_moments in smrt.h.
+template <class Lat, int N, class T, class Acc>
+struct MomentArgs {
+    StepArgs<Lat, T> s;
+    double *out;
+    long long ncells;
+    unsigned mask;
+    int line;    // 1: batched-line geometry (tiles), 0: box
+    int fixedx;
+};
+
+template <class Lat, int N, class T, class Acc>
+__global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc> m) {
+    constexpr int Nm = N < 3 ? 3 : N;
+    constexpr int Mm = nmom(Nm);
+    using C = Collide<Lat, N, T, Acc, false>;
+    using Cm = Collide<Lat, Nm, T, Acc, false>;
+    const StepArgs<Lat, T> &a = m.s;
+    T f[Lat::Q];
+    long long cell;
+    double ubar_x;
+    if (m.line) {
+        const int2 tile = a.tiles[blockIdx.x];
+        const InstanceInfo &in = a.inst[tile.x];
+        const int x = tile.y + threadIdx.x;
+        const int L = in.nx;
+        if (x >= L) return;
+        cell = in.cell_off + x;
+        ubar_x = double(a.c) * in.kx;
+        const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
+        const T *gr = gl + Lat::Q;
+        f[0] = a.fin[a.plane[0] + cell];
+        static_for<Lat::NP>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            static_for<2>([&](auto Sg) {
+                constexpr int sg = decltype(Sg)::value == 0 ? 1 : -1;
+                constexpr int i = 2 * p + 1 + decltype(Sg)::value;
+                const int xs = x - (sg * Lat::e(p, 0) + in.kx);
+                if (m.fixedx && xs < 0)
+                    f[i] = gl[i];
+                else if (m.fixedx && xs >= L)
+                    f[i] = gr[i];
+                else
+                    f[i] = a.fin[a.plane[i] + in.cell_off + wrap(xs, L)];
+            });
+        });
+    } else {
+        const int x = blockIdx.x * blockDim.x + threadIdx.x;
+        const int y = blockIdx.y, z = blockIdx.z;
+        if (x >= a.nx) return;
+        const long long row = a.nx, slab = row * a.ny;
+        cell = z * slab + y * row + x;
+        ubar_x = double(a.c) * a.kx;
+        f[0] = a.fin[a.plane[0] + cell];
+        static_for<Lat::NP>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            static_for<2>([&](auto Sg) {
+                constexpr int sg = decltype(Sg)::value == 0 ? 1 : -1;
+                constexpr int i = 2 * p + 1 + decltype(Sg)::value;
+                const int xs = wrap(x - (sg * Lat::e(p, 0) + a.kx), a.nx);
+                const int ys = wrap(y - (sg * Lat::e(p, 1) + a.ky), a.ny);
+                const int zs = wrap(z - (sg * Lat::e(p, 2) + a.kz), a.nz);
+                f[i] = a.fin[a.plane[i] + zs * slab + ys * row + xs];
+            });
+        });
+    }
+    Acc rho, u[3], th;
+    C::conserved(f, Acc(a.c), rho, u, th);
+    T v[Mm];
+    Cm::template absolute<Nm>(f, a.c, v);
+    const T ut[3] = {T(u[0]), T(u[1]), T(u[2])};
+    Cm::template to_local<Nm>(v, ut, T(th));
+    // undivide: d_beta = beta! td_beta
+    double d[Mm];
+    static_for<Mm>([&](auto A) {
+        constexpr int p = decltype(A)::value;
+        d[p] = double(v[p]) * mi_fact(p);
+    });
+    d[0] = double(rho);
+    const double thd = double(th);
+    double *o = m.out;
+    const long long nc = m.ncells;
+    long long r = 0;
+    if (m.mask & 0x1u) o[(r++) * nc + cell] = double(rho);
+    if (m.mask & 0x2u) {
+        o[(r++) * nc + cell] = double(u[0]) + ubar_x;
+        o[(r++) * nc + cell] = double(u[1]) + double(a.c) * a.ky;
+        o[(r++) * nc + cell] = double(u[2]) + double(a.c) * a.kz;
+    }
+    if (m.mask & 0x4u) o[(r++) * nc + cell] = thd;
+    if (m.mask & 0x8u) {
+        o[(r++) * nc + cell] = thd * d[mi_pos(2, 0, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 2, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 0, 2)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(1, 1, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(1, 0, 1)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 1, 1)];
+    }
+    if (m.mask & 0x10u) {
+        const double s = 0.5 * thd * sqrt(thd);
+        o[(r++) * nc + cell] = s * (d[mi_pos(3, 0, 0)] + d[mi_pos(1, 2, 0)] + d[mi_pos(1, 0, 2)]);
+        o[(r++) * nc + cell] = s * (d[mi_pos(2, 1, 0)] + d[mi_pos(0, 3, 0)] + d[mi_pos(0, 1, 2)]);
+        o[(r++) * nc + cell] = s * (d[mi_pos(2, 0, 1)] + d[mi_pos(0, 2, 1)] + d[mi_pos(0, 0, 3)]);
+    }
+    if (m.mask & 0x20u) {
+        static_for<Mm>([&](auto A) {
+            constexpr int p = decltype(A)::value;
+            o[(r + p) * nc + cell] = d[p];
+        });
+    }
+}
+
+// ------------------------------------------------------------------------------ equilibrium
+// f = order-N equilibrium of (rho, u_phys - u_bar, theta), computed in double, stored as T.
+template <class Lat, int N, class T>
+SMRT_HD void equilibrium_cell(double rho, const double (&u)[3], double theta, double c,
+                              const T (&wp)[Lat::NP + 1], double (&out)[Lat::Q]) {
+    using C = Collide<Lat, N, T, double, false>;
+    double ta[nmom(N)];
+    C::template equilibrium<double>(rho, u, theta, ta);
+    C::template rebuild<double>(ta, c, wp, out);
+}
+
+template <class Lat, int N, class T>
+__global__ void __launch_bounds__(128) fill_kernel(StepArgs<Lat, T> a, const double *rho,
+                                                   const double *u, const double *theta,
+                                                   long long ncells, int line) {
+    long long cell;
+    int kx;
+    if (line) {
+        const int2 tile = a.tiles[blockIdx.x];
+        const InstanceInfo &in = a.inst[tile.x];
+        const int x = tile.y + threadIdx.x;
+        if (x >= in.nx) return;
+        cell = in.cell_off + x;
+        kx = in.kx;
+    } else {
+        cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (cell >= ncells) return;
+        kx = a.kx;
+    }
+    const double uu[3] = {u[cell] - double(a.c) * kx, u[ncells + cell] - double(a.c) * a.ky,
+                          u[2 * ncells + cell] - double(a.c) * a.kz};
+    double out[Lat::Q];
+    equilibrium_cell<Lat, N, T>(rho[cell], uu, theta[cell], double(a.c), a.wp, out);
+    static_for<Lat::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        a.fout[a.plane[i] + cell] = T(out[i]);
+    });
+}
+
+// End-state populations of instance j: states[j] = (rho, u_phys, theta) left then right.
+template <class Lat, int N, class T>
+__global__ void ghost_kernel(StepArgs<Lat, T> a, const double *states, int ninst, T *ghosts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * ninst) return;
+    const int j = t / 2;
+    const double *s = states + 5 * t;
+    const double ub = double(a.c) * a.inst[j].kx;
+    const double uu[3] = {s[1] - ub, s[2] - double(a.c) * a.ky, s[3] - double(a.c) * a.kz};
+    double out[Lat::Q];
+    equilibrium_cell<Lat, N, T>(s[0], uu, s[4], double(a.c), a.wp, out);
+    static_for<Lat::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        ghosts[(long long)t * Lat::Q + i] = T(out[i]);
+    });
+}
+
+}  // namespace smrt

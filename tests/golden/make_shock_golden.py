@@ -1,0 +1,61 @@
+"""Write oracle reference profiles of 1D normal shocks to tests/golden/*.npz.
+
+Calls only ``oracle/`` and the shared input generators in ``synthetic.py``; nothing here
+touches the CUDA path. Usage:
+
+    python tests/golden/make_shock_golden.py ma3_d3q103_n4   # Ma = 3, 2048 cells, 20000 steps
+
+Each case stores, at the listed step counts, the moments of the pre-collision populations
+(rho, physical u_x, theta, q_x) on every cell, float64.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synthetic  # noqa: E402
+from oracle import lattice as L  # noqa: E402
+from oracle import shock as K  # noqa: E402
+from oracle import smrt as S  # noqa: E402
+
+CASES = {
+    # SMRT, Table 4 times, ell = 2 upstream cells, tanh width 20, theta2 = 1.2 reference
+    "ma3_d3q103_n4": dict(lattice="D3Q103", N=4, Ma=3.0, nx=2048, width=20.0,
+                          checkpoints=(2000, 20000)),
+}
+
+
+def run(name: str):
+    cfg = CASES[name]
+    lat = L.by_name(cfg["lattice"])
+    case = K.shock_case(lat, cfg["N"], cfg["Ma"], cfg["nx"])
+    st = case.states
+    nx, W = cfg["nx"], cfg["width"]
+    h = K.initial_state(case, synthetic.tanh_blend(nx, W, st["rho1"], st["rho2"]),
+                        synthetic.tanh_blend(nx, W, st["u1"], st["u2"]),
+                        synthetic.tanh_blend(nx, W, st["theta1"], st["theta2"]))
+    out = {"theta1": case.theta1, "k": case.k, "tau_ref": case.model.tau_ref}
+    t0 = time.time()
+    done = 0
+    for cp in cfg["checkpoints"]:
+        for _ in range(cp - done):
+            h = S.step(h, case.model, case.geom)
+        done = cp
+        m = S.macroscopic(h, case.model, case.geom)
+        for key in ("rho", "theta"):
+            out[f"{key}_{cp}"] = m[key]
+        out[f"u_{cp}"] = m["u"][0]
+        out[f"q_{cp}"] = m["q"][0]
+        print(f"{name}: step {cp} after {time.time() - t0:.0f} s", flush=True)
+    np.savez_compressed(os.path.join(HERE, f"{name}.npz"), **out)
+
+
+if __name__ == "__main__":
+    for n in sys.argv[1:] or list(CASES):
+        run(n)

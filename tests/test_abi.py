@@ -1,0 +1,103 @@
+"""The C ABI without a GPU: the library builds and loads, exports every symbol that
+include/smrt.h declares, its host-side helpers agree with the oracle, and argument validation
+rejects bad requests before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as OL
+from oracle import shock as OK
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_11086_gb300 import _ffi
+    from paper_2401_11086_gb300.build import build
+    build()
+    return _ffi.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "smrt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2401_11086_gb300 import _ffi
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_ffi.SIGNATURES)
+
+
+def test_error_strings(lib):
+    for s in range(7):
+        assert lib.lb_error_string(s)
+    assert lib.lb_error_string(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("name", ["D3Q39", "D3Q103"])
+def test_library_lattice_agrees_with_oracle(lib, name):
+    import paper_2401_11086_gb300 as P
+    d = P.lb_lattice_named(name)
+    o = OL.by_name(name)
+    assert d.q == o.q and d.degree == o.degree
+    assert abs(d.c - o.c) < 1e-13
+    key = {tuple(e): w for e, w in zip(o.e.tolist(), o.w)}
+    for e, w in zip(d.e.tolist(), d.w):
+        assert abs(key[tuple(e)] - w) < 1e-13 * max(w, 1e-3)
+
+
+@pytest.mark.parametrize("Ma", [1.2, 1.5, 3.0, 5.0, 7.0])
+def test_library_rankine_hugoniot_agrees_with_oracle(lib, Ma):
+    import paper_2401_11086_gb300 as P
+    th1 = OK.theta_scale(Ma)
+    left, right = P.lb_rankine_hugoniot(Ma, theta1=th1)
+    st = OK.rankine_hugoniot(Ma, theta1=th1)
+    assert abs(left["u"][0] - st["u1"]) < 1e-13 and abs(right["u"][0] - st["u2"]) < 1e-13
+    assert abs(right["rho"] - st["rho2"]) < 1e-13 and abs(right["theta"] - st["theta2"]) < 1e-13
+
+
+def _init(lib, e, w, c, degree, N=3, nx=8, ny=8, nz=8, prec=1, shift=(0, 0, 0), bc_x=0):
+    from paper_2401_11086_gb300 import _ffi
+    e = np.ascontiguousarray(e, dtype=np.int8)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    desc = _ffi.LbLatticeDesc(len(w), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                              w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), c, degree,
+                              (ctypes.c_int * 3)(*shift))
+    grid = _ffi.LbGridDesc(nx, ny, nz, 1, None, bc_x)
+    h = ctypes.c_void_p()
+    return lib.lb_init_lattice(ctypes.byref(h), ctypes.byref(desc), ctypes.byref(grid), N, prec, None)
+
+
+def test_validation_before_any_cuda_call(lib):
+    import paper_2401_11086_gb300 as P
+    d = P.lb_lattice_named("D3Q39")
+    bad = d.w.copy()
+    bad[5] *= 1.01                                   # not a quadrature any more
+    assert _init(lib, d.e, bad, d.c, 7) == 1
+    assert _init(lib, d.e, d.w, d.c * 1.001, 7) == 1  # wrong scale
+    assert _init(lib, d.e, d.w, d.c, 7, N=4) == 1     # degree 7 < 2N
+    assert _init(lib, d.e, d.w, d.c, 7, prec=9) == 1  # unknown precision
+    neg = d.w.copy()
+    neg[0] = -neg[0]
+    assert _init(lib, d.e, neg, d.c, 7) == 1
+    assert _init(lib, d.e, d.w, d.c, 7, ny=0) == 1
+    assert lib.lb_step(None, None, None, 1) == 1
+    assert lib.lb_moments(None, None, None, 1) == 1
+    assert lib.lb_poll_status(None, None) == 1
+    assert lib.lb_cells(None) == 0
+
+
+def test_unknown_lattice_is_unsupported(lib):
+    """A valid degree-11 rule the library has no kernel for (the paper's D3Q729)."""
+    o = OL.d3q729()
+    assert _init(lib, o.e[:103], o.w[:103], o.c, 11) in (1, 5)
+    assert lib.lb_lattice_named(b"D3Q729", None, None, None, None, None, 0) == 1

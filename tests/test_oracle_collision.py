@@ -234,3 +234,13 @@ def test_streaming_is_a_permutation(lats):
         assert np.allclose(np.sort(f[i].ravel()), np.sort(h[i].ravel()))
         sx, sy, sz = lat.e[i] + np.array([1, 0, 0])
         assert f[i][sz % 4, sy % 5, sx % 6] == h[i][0, 0, 0]
+
+
+def test_pull_cells_matches_stream(lats):
+    lat = lats["D3Q39"]
+    rng = np.random.default_rng(4)
+    h = rng.random((lat.q, 5, 6, 7))
+    geom = S.Geometry(shape=(5, 6, 7), shift=(1, 0, 0))
+    full = S.stream(h, lat, geom).reshape(lat.q, -1)
+    cells = rng.choice(5 * 6 * 7, size=20, replace=False)
+    np.testing.assert_array_equal(S.pull_cells(h, lat, geom, cells), full[:, cells])
