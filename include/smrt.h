@@ -12,9 +12,12 @@
  *          of the library (lb_state.u, lb_fill_equilibrium's u, lb_moments' u) are PHYSICAL
  *          (they include u_bar); theta is the temperature in units of the reference
  *          temperature ("energy units", Sec. 2).
- * State.   A state is the set of post-collision populations of every cell, structure of
- *          arrays: element  f[i * plane_stride + cell]  for population i (the caller's
- *          lattice order) and cell = instance_offset + (z * ny + y) * nx + x, x fastest.
+ * State.   A state is the set of post-collision populations of every cell, stored as their
+ *          deviations from the weights, df_i = f_i - w_i (the populations of the rest state
+ *          rho = 1, u = u_bar, theta = 1 are exactly w_i, so rounding acts only on the
+ *          deviation), structure of arrays: element  df[i * plane_stride + cell]  for population
+ *          i (the caller's lattice order) and cell = instance_offset + (z * ny + y) * nx + x,
+ *          x fastest.
  *          Instances (batched 1D problems) are concatenated in order. plane_stride and the
  *          element count of a state are given by lb_plane_stride / lb_state_elems.
  *          The element type is double for LB_F64 and float otherwise.

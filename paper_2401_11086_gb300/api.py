@@ -105,8 +105,14 @@ class Context:
         return torch.zeros(self.state_elems, dtype=self.dtype, device=self.device)
 
     def planes(self, f):
-        """(q, cells) view of a state tensor (drops the alignment padding of each plane)."""
+        """(q, cells) view of a state tensor (drops the alignment padding of each plane).
+        A state stores deviations df_i = f_i - w_i (see include/smrt.h)."""
         return f.view(self.lattice.q, self.plane_stride)[:, : self.cells]
+
+    @property
+    def weights(self):
+        """w_i in the caller's velocity order (add to a state's planes to get f_i)."""
+        return np.asarray(self.lattice.w, dtype=np.float64)
 
     def close(self):
         if self.handle:

@@ -66,8 +66,13 @@ struct Collide {
     static constexpr int M = nmom(N);
     static constexpr int KT = ntau(N);
 
-    // a2: conserved sums, in Acc.
-    SMRT_HD static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc (&u)[3], Acc &theta) {
+    // a2: conserved sums, in Acc. The state holds deviations df_i = f_i - w_i; the quadrature
+    // gives sum w_i = 1, sum w_i xi_i = 0, sum w_i |xi_i|^2 = 3, so
+    //   rho - 1 = sum df_i,  rho u = c sum e_i df_i,  E - 3 = c^2 sum |e_i|^2 df_i,
+    //   theta - 1 = (E - 3 - 3 (rho - 1) - rho |u|^2) / (3 rho),
+    // which keeps rho - 1 and theta - 1 free of cancellation.
+    SMRT_HD static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
+                                  Acc &theta, Acc &thm1) {
         Acc r = Acc(f[0]), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
         static_for<NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
@@ -81,12 +86,15 @@ struct Collide {
             if constexpr (e2 != 0) j2 = fma(Acc(e2), dp, j2);
             en = fma(Acc(ee), sp, en);
         });
-        rho = r;
-        const Acc ir = Acc(1) / r;
+        rhom1 = r;
+        rho = Acc(1) + r;
+        const Acc ir = Acc(1) / rho;
         u[0] = c * j0 * ir;
         u[1] = c * j1 * ir;
         u[2] = c * j2 * ir;
-        theta = (c * c * en * ir - (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) * Acc(1.0 / 3.0);
+        const Acc uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        thm1 = (c * c * en - Acc(3) * r - rho * uu) * ir * Acc(1.0 / 3.0);
+        theta = Acc(1) + thm1;
     }
 
     // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma,
@@ -135,11 +143,11 @@ struct Collide {
 
     // a4: td_beta = d_beta / beta! = theta^(-|beta|/2) [T(-u, 2 - theta) ta]_beta
     template <int Nm>
-    SMRT_HD static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta) {
+    SMRT_HD static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta, T thm1) {
         T G[3][Nm + 1];
         static_for<3>([&](auto K) {
             constexpr int k = decltype(K)::value;
-            maxwell_divided<Nm, T>(G[k], -u[k], T(1) - theta);
+            maxwell_divided<Nm, T>(G[k], -u[k], -thm1);
         });
         binomial_divided<Nm, T>(v, G);
         const T is = T(1) / sqrt(theta);
@@ -192,33 +200,36 @@ struct Collide {
     }
 
     // ta^eq_alpha = rho prod_k g_{alpha_k}(u_k, theta) / alpha_k!  (3D product of the
-    // Appendix B closed form), computed in U.
+    // Appendix B closed form), minus the coefficients of f = w_i (1 in slot 0), in U.
     template <class U>
-    SMRT_HD static void equilibrium(U rho, const U (&u)[3], U theta, U (&ta)[M]) {
+    SMRT_HD static void equilibrium(U rho, U rhom1, const U (&u)[3], U thm1, U (&ta)[M]) {
         U G[3][N + 1];
         static_for<3>([&](auto K) {
             constexpr int k = decltype(K)::value;
-            maxwell_divided<N, U>(G[k], u[k], theta - U(1));
+            maxwell_divided<N, U>(G[k], u[k], thm1);
         });
         static_for<M>([&](auto A) {
             constexpr int p = decltype(A)::value;
             ta[p] = rho * G[0][mi_comp(p, 0)] * G[1][mi_comp(p, 1)] * G[2][mi_comp(p, 2)];
         });
+        ta[0] = rhom1;
     }
 
-    // The whole collision: f (pre-collision, library order) -> f (post-collision).
+    // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
     // Returns false when rho or theta is not positive (or NaN).
     SMRT_HD static bool collide(T (&f)[Q], const T (&wp)[NP + 1], T c, const double *tauA,
                                 const double *tauB) {
-        Acc rho_a, u_a[3], th_a;
-        conserved(f, Acc(c), rho_a, u_a, th_a);
+        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a;
+        conserved(f, Acc(c), rho_a, rhom1_a, u_a, th_a, thm1_a);
         const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
-        const T rho = T(rho_a), theta = T(th_a);
+        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
         const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
 
+        // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
         T v[M];
         absolute<N>(f, c, v);
-        to_local<N>(v, u, theta);
+        v[0] = rho;
+        to_local<N>(v, u, theta, thm1);
 
         // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u
         T s[KT];
@@ -245,18 +256,19 @@ struct Collide {
         T G[3][N + 1];
         static_for<3>([&](auto K) {
             constexpr int k = decltype(K)::value;
-            maxwell_divided<N, T>(G[k], u[k], theta - T(1));
+            maxwell_divided<N, T>(G[k], u[k], thm1);
         });
         binomial_divided<N, T>(v, G);
 
         if constexpr (!Split) {
+            v[0] = T(rhom1_a);  // deviation from the coefficients of w_i
             T out[Q];
             rebuild<T>(v, c, wp, out);
             static_for<Q>([&](auto I) { f[decltype(I)::value] = out[decltype(I)::value]; });
         } else {
             // equilibrium part in Acc from the Acc moments, non-equilibrium part in T
             Acc teq[M];
-            equilibrium<Acc>(rho_a, u_a, th_a, teq);
+            equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
             Acc oeq[Q];
             rebuild<Acc>(teq, Acc(c), wp, oeq);
             T oneq[Q];
@@ -283,7 +295,7 @@ __global__ void __launch_bounds__(128) step_box_kernel(StepArgs<Lat, T> a) {
     const long long row = (long long)a.nx;
     const long long slab = row * a.ny;
     T f[Lat::Q];
-    f[0] = a.fin[a.plane[0] + z * slab + y * row + x];
+    f[0] = a.fin[a.plane[0] + wrap(z - a.kz, a.nz) * slab + wrap(y - a.ky, a.ny) * row + wrap(x - a.kx, a.nx)];
     static_for<Lat::NP>([&](auto P) {
         constexpr int p = decltype(P)::value;
         static_for<2>([&](auto Sg) {
@@ -318,7 +330,13 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
     const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
     const T *gr = gl + Lat::Q;
     T f[Lat::Q];
-    f[0] = a.fin[a.plane[0] + base + x];
+    {  // the rest population streams by k as well
+        const int xs = x - in.kx;
+        if constexpr (FixedX)
+            f[0] = xs < 0 ? gl[0] : (xs >= L ? gr[0] : a.fin[a.plane[0] + base + xs]);
+        else
+            f[0] = a.fin[a.plane[0] + base + wrap(xs, L)];
+    }
     static_for<Lat::NP>([&](auto P) {
         constexpr int p = decltype(P)::value;
         static_for<2>([&](auto Sg) {
@@ -377,7 +395,15 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
         ubar_x = double(a.c) * in.kx;
         const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
         const T *gr = gl + Lat::Q;
-        f[0] = a.fin[a.plane[0] + cell];
+        {
+            const int xs = x - in.kx;
+            if (m.fixedx && xs < 0)
+                f[0] = gl[0];
+            else if (m.fixedx && xs >= L)
+                f[0] = gr[0];
+            else
+                f[0] = a.fin[a.plane[0] + in.cell_off + wrap(xs, L)];
+        }
         static_for<Lat::NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
             static_for<2>([&](auto Sg) {
@@ -399,7 +425,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
         const long long row = a.nx, slab = row * a.ny;
         cell = z * slab + y * row + x;
         ubar_x = double(a.c) * a.kx;
-        f[0] = a.fin[a.plane[0] + cell];
+        f[0] = a.fin[a.plane[0] + wrap(z - a.kz, a.nz) * slab + wrap(y - a.ky, a.ny) * row + wrap(x - a.kx, a.nx)];
         static_for<Lat::NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
             static_for<2>([&](auto Sg) {
@@ -412,12 +438,13 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
             });
         });
     }
-    Acc rho, u[3], th;
-    C::conserved(f, Acc(a.c), rho, u, th);
+    Acc rho, rhom1, u[3], th, thm1;
+    C::conserved(f, Acc(a.c), rho, rhom1, u, th, thm1);
     T v[Mm];
     Cm::template absolute<Nm>(f, a.c, v);
+    v[0] = T(rho);
     const T ut[3] = {T(u[0]), T(u[1]), T(u[2])};
-    Cm::template to_local<Nm>(v, ut, T(th));
+    Cm::template to_local<Nm>(v, ut, T(th), T(thm1));
     // undivide: d_beta = beta! td_beta
     double d[Mm];
     static_for<Mm>([&](auto A) {
@@ -459,13 +486,13 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
 }
 
 // ------------------------------------------------------------------------------ equilibrium
-// f = order-N equilibrium of (rho, u_phys - u_bar, theta), computed in double, stored as T.
+// df = order-N equilibrium of (rho, u_phys - u_bar, theta) minus w_i, in double, stored as T.
 template <class Lat, int N, class T>
 SMRT_HD void equilibrium_cell(double rho, const double (&u)[3], double theta, double c,
                               const T (&wp)[Lat::NP + 1], double (&out)[Lat::Q]) {
     using C = Collide<Lat, N, T, double, false>;
     double ta[nmom(N)];
-    C::template equilibrium<double>(rho, u, theta, ta);
+    C::template equilibrium<double>(rho, rho - 1.0, u, theta - 1.0, ta);
     C::template rebuild<double>(ta, c, wp, out);
 }
 
