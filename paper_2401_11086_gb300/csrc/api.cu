@@ -272,6 +272,8 @@ extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell
         for (int k = 0; k < nt; ++k) {
             in.tauA[k] = maxwell ? tau[k] * rho_ref : 0.0;
             in.tauB[k] = maxwell ? 0.5 : tau[k] + 0.5;
+            in.tauAf[k] = (float)in.tauA[k];
+            in.tauBf[k] = (float)in.tauB[k];
         }
         if (c->view.fixedx) {
             double *s = &c->h_states[(size_t)j * 10];

@@ -27,6 +27,14 @@
 namespace smrt {
 
 #define SMRT_HD __host__ __device__ __forceinline__
+#define SMRT_D __device__ __forceinline__
+
+// Reciprocal and reciprocal square root: correctly rounded reciprocal and the hardware
+// reciprocal square root for float (within 2 ulp), exact division for double.
+SMRT_D float rcp(float x) { return __frcp_rn(x); }
+SMRT_D double rcp(double x) { return 1.0 / x; }
+SMRT_D float rsq(float x) { return rsqrtf(x); }
+SMRT_D double rsq(double x) { return 1.0 / sqrt(x); }
 
 // ------------------------------------------------------------------ compile-time loops
 template <int V>

@@ -36,7 +36,22 @@ struct InstanceInfo {
     int kx;              // frame shift along x (u_bar_x = c kx)
     double tauA[kMaxTau];
     double tauB[kMaxTau];
+    float tauAf[kMaxTau];  // the same in float, read by the float kernels
+    float tauBf[kMaxTau];
 };
+
+template <class T>
+SMRT_D const T *tau_a(const InstanceInfo &in);
+template <>
+SMRT_D const double *tau_a<double>(const InstanceInfo &in) { return in.tauA; }
+template <>
+SMRT_D const float *tau_a<float>(const InstanceInfo &in) { return in.tauAf; }
+template <class T>
+SMRT_D const T *tau_b(const InstanceInfo &in);
+template <>
+SMRT_D const double *tau_b<double>(const InstanceInfo &in) { return in.tauB; }
+template <>
+SMRT_D const float *tau_b<float>(const InstanceInfo &in) { return in.tauBf; }
 
 template <class Lat, class T>
 struct StepArgs {
@@ -54,8 +69,8 @@ struct StepArgs {
 };
 
 template <class T>
-SMRT_HD T rcp_tau(double A, double B, T rho) {
-    return rho / (T(A) + T(B) * rho);
+SMRT_D T rcp_tau(T A, T B, T rho) {
+    return rho * rcp(fma(B, rho, A));
 }
 
 // ------------------------------------------------------------------------------ collision
@@ -71,7 +86,7 @@ struct Collide {
     //   rho - 1 = sum df_i,  rho u = c sum e_i df_i,  E - 3 = c^2 sum |e_i|^2 df_i,
     //   theta - 1 = (E - 3 - 3 (rho - 1) - rho |u|^2) / (3 rho),
     // which keeps rho - 1 and theta - 1 free of cancellation.
-    SMRT_HD static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
+    SMRT_D static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
                                   Acc &theta, Acc &thm1) {
         Acc r = Acc(f[0]), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
         static_for<NP>([&](auto P) {
@@ -88,7 +103,7 @@ struct Collide {
         });
         rhom1 = r;
         rho = Acc(1) + r;
-        const Acc ir = Acc(1) / rho;
+        const Acc ir = rcp(rho);
         u[0] = c * j0 * ir;
         u[1] = c * j1 * ir;
         u[2] = c * j2 * ir;
@@ -100,7 +115,13 @@ struct Collide {
     // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma,
     // R_gamma = sum_i f_i e_i^gamma, pairs folded: even |gamma| use f+ + f-, odd use f+ - f-.
     template <int Nm>
-    SMRT_HD static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)]) {
+    SMRT_D static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)]) {
+        T Rc[nmom(Nm)];
+        absolute<Nm>(f, c, ta, Rc);
+    }
+    // ... and the scaled raw moments Rc_gamma = c^|gamma| sum_i df_i e_i^gamma themselves
+    template <int Nm>
+    SMRT_D static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)], T (&Rc)[nmom(Nm)]) {
         constexpr int Mm = nmom(Nm);
         T S[NP], D[NP];
         static_for<NP>([&](auto P) {
@@ -111,7 +132,6 @@ struct Collide {
         T cp[Nm + 1];
         cp[0] = T(1);
         static_for<Nm>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
-        T Rc[Mm];
         static_for<Mm>([&](auto G) {
             constexpr int g = decltype(G)::value;
             constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
@@ -143,14 +163,14 @@ struct Collide {
 
     // a4: td_beta = d_beta / beta! = theta^(-|beta|/2) [T(-u, 2 - theta) ta]_beta
     template <int Nm>
-    SMRT_HD static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta, T thm1) {
+    SMRT_D static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta, T thm1) {
         T G[3][Nm + 1];
         static_for<3>([&](auto K) {
             constexpr int k = decltype(K)::value;
             maxwell_divided<Nm, T>(G[k], -u[k], -thm1);
         });
         binomial_divided<Nm, T>(v, G);
-        const T is = T(1) / sqrt(theta);
+        const T is = rsq(theta);
         T sp[Nm + 1];
         sp[0] = T(1);
         static_for<Nm>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * is; });
@@ -163,7 +183,7 @@ struct Collide {
     // a7 + a8 helper: values f'_i = w_i sum_gamma P_gamma e_i^gamma with
     // P_gamma = c^|gamma| sum_alpha hfull(alpha, gamma) ta'_alpha; U is the arithmetic type.
     template <class U>
-    SMRT_HD static void rebuild(const U (&ta)[M], U c, const T (&wp)[NP + 1], U (&out)[Q]) {
+    SMRT_D static void rebuild(const U (&ta)[M], U c, const T (&wp)[NP + 1], U (&out)[Q]) {
         U cp[N + 1];
         cp[0] = U(1);
         static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
@@ -202,7 +222,7 @@ struct Collide {
     // ta^eq_alpha = rho prod_k g_{alpha_k}(u_k, theta) / alpha_k!  (3D product of the
     // Appendix B closed form), minus the coefficients of f = w_i (1 in slot 0), in U.
     template <class U>
-    SMRT_HD static void equilibrium(U rho, U rhom1, const U (&u)[3], U thm1, U (&ta)[M]) {
+    SMRT_D static void equilibrium(U rho, U rhom1, const U (&u)[3], U thm1, U (&ta)[M]) {
         U G[3][N + 1];
         static_for<3>([&](auto K) {
             constexpr int k = decltype(K)::value;
@@ -217,17 +237,31 @@ struct Collide {
 
     // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
     // Returns false when rho or theta is not positive (or NaN).
-    SMRT_HD static bool collide(T (&f)[Q], const T (&wp)[NP + 1], T c, const double *tauA,
-                                const double *tauB) {
+    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], T c, const T *tauA,
+                               const T *tauB) {
+        // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
+        T v[M], Rc[M];
+        absolute<N>(f, c, v, Rc);
         Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a;
-        conserved(f, Acc(c), rho_a, rhom1_a, u_a, th_a, thm1_a);
+        if constexpr (std::is_same<Acc, T>::value) {
+            // a2 from the raw moments already formed: rho - 1 = Rc_0, rho u = Rc_1,
+            // E - 3 = tr Rc_2
+            rhom1_a = Rc[0];
+            rho_a = T(1) + rhom1_a;
+            const T ir = rcp(rho_a);
+            u_a[0] = Rc[mi_pos(1, 0, 0)] * ir;
+            u_a[1] = Rc[mi_pos(0, 1, 0)] * ir;
+            u_a[2] = Rc[mi_pos(0, 0, 1)] * ir;
+            const T uu = u_a[0] * u_a[0] + u_a[1] * u_a[1] + u_a[2] * u_a[2];
+            const T em3 = Rc[mi_pos(2, 0, 0)] + Rc[mi_pos(0, 2, 0)] + Rc[mi_pos(0, 0, 2)];
+            thm1_a = (em3 - T(3) * rhom1_a - rho_a * uu) * ir * T(1.0 / 3.0);
+            th_a = T(1) + thm1_a;
+        } else {
+            conserved(f, Acc(c), rho_a, rhom1_a, u_a, th_a, thm1_a);
+        }
         const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
         const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
         const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
-
-        // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
-        T v[M];
-        absolute<N>(f, c, v);
         v[0] = rho;
         to_local<N>(v, u, theta, thm1);
 
@@ -240,7 +274,7 @@ struct Collide {
         static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
 
         // a6: back to the absolute frame: scale by theta^(|beta|/2), transform with T(u, theta)
-        const T sq = sqrt(theta);
+        const T sq = theta * rsq(theta);
         T sp[N + 1];
         sp[0] = T(1);
         static_for<N>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * sq; });
@@ -307,7 +341,7 @@ __global__ void __launch_bounds__(128) step_box_kernel(StepArgs<Lat, T> a) {
             f[i] = a.fin[a.plane[i] + zs * slab + ys * row + xs];
         });
     });
-    const bool ok = C::collide(f, a.wp, a.c, a.inst[0].tauA, a.inst[0].tauB);
+    const bool ok = C::collide(f, a.wp, a.c, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]));
     if (!ok) atomicOr(a.health, 1u);
     const long long cell = z * slab + y * row + x;
     static_for<Lat::Q>([&](auto I) {
@@ -355,7 +389,7 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
             }
         });
     });
-    const bool ok = C::collide(f, a.wp, a.c, in.tauA, in.tauB);
+    const bool ok = C::collide(f, a.wp, a.c, tau_a<T>(in), tau_b<T>(in));
     if (!ok) atomicOr(a.health, 1u);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -488,7 +522,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
 // ------------------------------------------------------------------------------ equilibrium
 // df = order-N equilibrium of (rho, u_phys - u_bar, theta) minus w_i, in double, stored as T.
 template <class Lat, int N, class T>
-SMRT_HD void equilibrium_cell(double rho, const double (&u)[3], double theta, double c,
+SMRT_D void equilibrium_cell(double rho, const double (&u)[3], double theta, double c,
                               const T (&wp)[Lat::NP + 1], double (&out)[Lat::Q]) {
     using C = Collide<Lat, N, T, double, false>;
     double ta[nmom(N)];
