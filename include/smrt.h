@@ -160,6 +160,29 @@ lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
  * the bits above. Errors: LB_ERR_INVALID, LB_ERR_CUDA. */
 lb_status lb_moments(lb_ctx *ctx, const void *f, double *out, unsigned which_mask);
 
+/* lb_step_adjoint -- one step of the discrete adjoint (reverse mode) of lb_step, for gradients
+ * of a loss L with respect to the state and to the relaxation times of Eq. SMRT. With
+ * h^{t+1} = C(S h^t) (S: pull streaming of Sec. 3, C: per-cell collision):
+ *   lam_t = S^T J_C(S h^t)^T lam_next,   dtau[k] += sum_cells (d h^{t+1} / d tau_c,k)^T lam_next.
+ * f_t: the forward state h^t entering the step (a state of this context, device).
+ * lam_next: dL/dh^{t+1}, lam_t: dL/dh^t (output, overwritten): device doubles with the state
+ * layout (lb_state_elems values; plane i = population i). dtau: device doubles, one per (n,m)
+ * in lb_set_relaxation's order, ACCUMULATED (+=) -- derivatives with respect to the continuous
+ * times tau_c,nm. Arithmetic is double whatever the precision of f_t. Populations pulled from
+ * beyond a fixed x end are constants (no gradient). The per-block gradient partials live in a
+ * scratch array owned by the context; calls on one context must not overlap.
+ * Errors: LB_ERR_INVALID (null, lam_next overlapping lam_t, relaxation unset), LB_ERR_CUDA. */
+lb_status lb_step_adjoint(lb_ctx *ctx, const void *f_t, const double *lam_next, double *lam_t,
+                          double *dtau);
+
+/* lb_moments_adjoint -- reverse mode of lb_moments for the row groups LB_MOM_RHO, LB_MOM_U,
+ * LB_MOM_THETA and LB_MOM_Q: given gbar = dL/d(moments) in lb_moments' layout for which_mask
+ * (rows x lb_cells doubles, device), writes lam = dL/df (device doubles, state layout,
+ * overwritten), including the transpose of the streaming that lb_moments applies.
+ * Errors: LB_ERR_INVALID (null, empty mask or a row group without an adjoint), LB_ERR_CUDA. */
+lb_status lb_moments_adjoint(lb_ctx *ctx, const void *f, const double *gbar, unsigned which_mask,
+                             double *lam);
+
 /* lb_poll_status -- synchronise the context's stream, return and clear its health word.
  * Returns LB_ERR_UNSTABLE / LB_ERR_TIMEOUT when the corresponding bit was set, LB_ERR_CUDA
  * when the stream reports an error, LB_OK otherwise. health_flags may be NULL. */

@@ -153,6 +153,8 @@ def lb_init_lattice(lattice: LatticeDesc, nx: int, ny: int = 1, nz: int = 1, N: 
 def lb_set_relaxation(ctx: Context, tau, maxwell_molecule_law: bool = True, rho_ref: float = 1.0,
                       left=None, right=None, instance: int = -1):
     t = np.ascontiguousarray(tau, dtype=np.float64)
+    ctx.relax_args = dict(maxwell_molecule_law=maxwell_molecule_law, rho_ref=rho_ref, left=left,
+                          right=right, instance=instance)
     L, R = _state(left), _state(right)
     _check(_ffi.lib().lb_set_relaxation(ctx.handle, t.ctypes.data_as(ctypes.POINTER(c_double)),
                                         int(bool(maxwell_molecule_law)), float(rho_ref),
@@ -201,6 +203,22 @@ def lb_moments(ctx: Context, f, mask: int = LB_MOM_RHO | LB_MOM_U | LB_MOM_THETA
     _check(_ffi.lib().lb_moments(ctx.handle, _ptr(f, ctx.dtype), _ptr(out, torch.float64), c_uint(mask)),
            "lb_moments")
     return out
+
+
+def lb_step_adjoint(ctx: Context, f_t, lam_next, lam_t, dtau):
+    """lam_t = adjoint of one step at forward state f_t applied to lam_next; dtau += gradient."""
+    import torch
+    _check(_ffi.lib().lb_step_adjoint(ctx.handle, _ptr(f_t, ctx.dtype), _ptr(lam_next, torch.float64),
+                                      _ptr(lam_t, torch.float64), _ptr(dtau, torch.float64)),
+           "lb_step_adjoint")
+    return lam_t
+
+
+def lb_moments_adjoint(ctx: Context, f, gbar, mask: int, lam):
+    import torch
+    _check(_ffi.lib().lb_moments_adjoint(ctx.handle, _ptr(f, ctx.dtype), _ptr(gbar, torch.float64),
+                                         c_uint(mask), _ptr(lam, torch.float64)), "lb_moments_adjoint")
+    return lam
 
 
 def lb_poll_status(ctx: Context):

@@ -30,6 +30,7 @@ struct lb_ctx {
     lb_precision prec;
     size_t elem;  // bytes per population value
     const KernelSet *ks;
+    const AdjointSet *as;
     CtxView view;
     std::vector<int> perm;  // library index -> caller index
     std::vector<int> nx_inst;
@@ -44,6 +45,7 @@ struct lb_ctx {
     void *d_ghosts;
     double *d_states;
     unsigned *d_health;
+    double *d_partials;  // per-block relaxation-time gradients of lb_step_adjoint
 };
 
 namespace {
@@ -90,6 +92,7 @@ void free_tables(lb_ctx *c) {
     cudaFree(c->d_ghosts);
     cudaFree(c->d_states);
     cudaFree(c->d_health);
+    cudaFree(c->d_partials);
 }
 
 }  // namespace
@@ -121,11 +124,13 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         c->np = D3Q39::NP;
         for (int k = 0; k < 3; ++k) reach[k] = max_reach<D3Q39>(k);
         c->ks = prec == LB_F64 ? kernels_d3q39_p0(N) : (prec == LB_F32 ? kernels_d3q39_p1(N) : kernels_d3q39_p2(N));
+        c->as = adjoints_d3q39(N, prec);
     } else if (match_set<D3Q103>(lat, c->perm)) {
         c->kind = 1;
         c->np = D3Q103::NP;
         for (int k = 0; k < 3; ++k) reach[k] = max_reach<D3Q103>(k);
         c->ks = prec == LB_F64 ? kernels_d3q103_p0(N) : (prec == LB_F32 ? kernels_d3q103_p1(N) : kernels_d3q103_p2(N));
+        c->as = adjoints_d3q103(N, prec);
     } else {
         delete c;
         return LB_ERR_UNSUPPORTED;
@@ -222,6 +227,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghosts, c->elem * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_states, sizeof(double) * 10 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_health, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * kMaxTau * std::max(1LL, adj_blocks(v)));
     if (e != cudaSuccess) {
         free_tables(c);
         delete c;
@@ -275,6 +281,8 @@ extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell
             in.tauAf[k] = (float)in.tauA[k];
             in.tauBf[k] = (float)in.tauB[k];
         }
+        in.dAdt = maxwell ? rho_ref : 0.0;
+        in.dBdt = maxwell ? 0.0 : 1.0;
         if (c->view.fixedx) {
             double *s = &c->h_states[(size_t)j * 10];
             const lb_state *st[2] = {left, right};
@@ -337,6 +345,23 @@ extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
 extern "C" lb_status lb_moments(lb_ctx *c, const void *f, double *out, unsigned mask) {
     if (!c || !f || !out || mask == 0 || (mask & ~0x3fu)) return LB_ERR_INVALID;
     return cuda_status(c->ks->moments(c->view, f, out, mask));
+}
+
+extern "C" lb_status lb_step_adjoint(lb_ctx *c, const void *f_t, const double *lam_next, double *lam_t,
+                                     double *dtau) {
+    if (!c || !f_t || !lam_next || !lam_t || !dtau || lam_next == lam_t) return LB_ERR_INVALID;
+    if (!c->relax_set || !c->as) return c->as ? LB_ERR_INVALID : LB_ERR_UNSUPPORTED;
+    const size_t bytes = sizeof(double) * lb_state_elems(c);
+    const char *a0 = reinterpret_cast<const char *>(lam_next), *b0 = reinterpret_cast<const char *>(lam_t);
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;
+    return cuda_status(c->as->step(c->view, f_t, lam_next, lam_t, c->d_partials, dtau));
+}
+
+extern "C" lb_status lb_moments_adjoint(lb_ctx *c, const void *f, const double *gbar, unsigned mask, double *lam) {
+    if (!c || !f || !gbar || !lam || mask == 0) return LB_ERR_INVALID;
+    if (mask & ~(LB_MOM_RHO | LB_MOM_U | LB_MOM_THETA | LB_MOM_Q)) return LB_ERR_INVALID;
+    if (!c->as) return LB_ERR_UNSUPPORTED;
+    return cuda_status(c->as->moments(c->view, f, gbar, mask, lam));
 }
 
 extern "C" lb_status lb_poll_status(lb_ctx *c, unsigned *flags) {

@@ -133,3 +133,81 @@ const KernelSet *kernel_set() {
 }
 
 }  // namespace smrt
+
+#include "adjoint_kernels.cuh"
+
+namespace smrt {
+
+using AdjStepFn = cudaError_t (*)(const CtxView &, const void *f, const double *lam_next, double *lam_t,
+                                  double *partials, double *dtau);
+using AdjMomentsFn = cudaError_t (*)(const CtxView &, const void *f, const double *gbar, unsigned mask,
+                                     double *lam);
+struct AdjointSet {
+    AdjStepFn step;
+    AdjMomentsFn moments;
+};
+const AdjointSet *adjoints_d3q39(int N, int precision);
+const AdjointSet *adjoints_d3q103(int N, int precision);
+
+template <class Lat, class T>
+AdjArgs<Lat, T> make_adj_args(const CtxView &v, const void *f) {
+    AdjArgs<Lat, T> A;
+    A.s = make_args<Lat, T>(v, f, nullptr);
+    for (int p = 0; p <= Lat::NP; ++p) A.wpd[p] = v.wp[p];
+    A.c = v.c;
+    A.line = v.line;
+    A.fixedx = v.fixedx;
+    A.ncells = v.ncells;
+    A.mask = 0;
+    A.lam_in = nullptr;
+    A.lam_out = nullptr;
+    A.partials = nullptr;
+    return A;
+}
+
+inline long long adj_blocks(const CtxView &v) {
+    return v.line ? (long long)v.ntiles : (long long)((v.nx + kTile - 1) / kTile) * v.ny * v.nz;
+}
+
+template <class Lat, int N, class T>
+cudaError_t launch_adj_step(const CtxView &v, const void *f, const double *lam_next, double *lam_t,
+                            double *partials, double *dtau) {
+    AdjArgs<Lat, T> A = make_adj_args<Lat, T>(v, f);
+    A.lam_in = lam_next;
+    A.lam_out = lam_t;
+    A.partials = partials;
+    if (v.line) {
+        adjoint_step_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(A);
+    } else {
+        const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
+        adjoint_step_kernel<Lat, N, T><<<grid, kTile, 0, v.stream>>>(A);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_partials_kernel<<<1, 32, 0, v.stream>>>(partials, adj_blocks(v), ntau(N), dtau);
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, class T>
+cudaError_t launch_adj_moments(const CtxView &v, const void *f, const double *gbar, unsigned mask, double *lam) {
+    AdjArgs<Lat, T> A = make_adj_args<Lat, T>(v, f);
+    A.lam_in = gbar;
+    A.lam_out = lam;
+    A.mask = mask;
+    if (v.line) {
+        adjoint_moments_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(A);
+    } else {
+        const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
+        adjoint_moments_kernel<Lat, N, T><<<grid, kTile, 0, v.stream>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+template <class Lat, int N, int P>
+const AdjointSet *adjoint_set() {
+    using T = typename std::conditional<P == 0, double, float>::type;
+    static const AdjointSet as = {&launch_adj_step<Lat, N, T>, &launch_adj_moments<Lat, N, T>};
+    return &as;
+}
+
+}  // namespace smrt

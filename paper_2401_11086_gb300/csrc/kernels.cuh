@@ -38,6 +38,7 @@ struct InstanceInfo {
     double tauB[kMaxTau];
     float tauAf[kMaxTau];  // the same in float, read by the float kernels
     float tauBf[kMaxTau];
+    double dAdt, dBdt;     // d tauA / d tau_c and d tauB / d tau_c (adjoint)
 };
 
 template <class T>

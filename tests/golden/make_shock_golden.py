@@ -3,7 +3,8 @@
 Calls only ``oracle/`` and the shared input generators in ``synthetic.py``; nothing here
 touches the CUDA path. Usage:
 
-    python tests/golden/make_shock_golden.py ma3_d3q103_n4   # Ma = 3, 2048 cells, 20000 steps
+    python tests/golden/make_shock_golden.py ma3_d3q103_n4          # Ma = 3, 2048 cells, 20000 steps
+    python tests/golden/make_shock_golden.py ma5_d3q103_n4_target   # Ma = 5, 1024 cells, 5000 steps
 
 Each case stores, at the listed step counts, the moments of the pre-collision populations
 (rho, physical u_x, theta, q_x) on every cell, float64.
@@ -28,6 +29,9 @@ CASES = {
     # SMRT, Table 4 times, ell = 2 upstream cells, tanh width 20, theta2 = 1.2 reference
     "ma3_d3q103_n4": dict(lattice="D3Q103", N=4, Ma=3.0, nx=2048, width=20.0,
                           checkpoints=(2000, 20000)),
+    # target of the differentiable shock: Ma = 5, 1024 cells, Table 4 times, 5000 steps
+    "ma5_d3q103_n4_target": dict(lattice="D3Q103", N=4, Ma=5.0, nx=1024, width=10.0,
+                                 checkpoints=(5000,)),
 }
 
 

@@ -1,0 +1,186 @@
+"""The adjoint kernels (lb_step_adjoint, lb_moments_adjoint) and the checkpointed autograd run
+against the oracle's discrete adjoint and against central finite differences."""
+import os
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import adjoint as OA
+from oracle import lattice as OL
+from oracle import shock as OK
+from oracle import smrt as OS
+from _lb import download, lib_from_oracle, upload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2401_11086_gb300 as P  # noqa: E402
+from paper_2401_11086_gb300.autograd import relaxation_run  # noqa: E402
+
+
+def _plain_up(ctx, g, idx):
+    """A gradient field (no weight shift) from oracle layout to a device state-shaped tensor."""
+    out = torch.zeros(ctx.state_elems, dtype=torch.float64, device=ctx.device)
+    out.view(ctx.lattice.q, ctx.plane_stride)[:, : ctx.cells] = torch.from_numpy(
+        np.ascontiguousarray(np.asarray(g).reshape(g.shape[0], -1)[idx])).cuda()
+    return out
+
+
+def _plain_down(ctx, t, idx):
+    arr = t.view(ctx.lattice.q, ctx.plane_stride)[:, : ctx.cells].cpu().numpy()
+    out = np.empty_like(arr)
+    out[idx] = arr
+    return out
+
+
+def _setup(name, N, Ma, nx, prec, width=4.0):
+    olat = OL.by_name(name)
+    d = P.lb_lattice_named(name)
+    idx = lib_from_oracle(olat, d)
+    case = OK.shock_case(olat, N, Ma, nx)
+    st = case.states
+    h0 = OK.initial_state(case, *[synthetic.tanh_blend(nx, width, st[k + "1"], st[k + "2"])
+                                  for k in ("rho", "u", "theta")])
+    left, right = P.lb_rankine_hugoniot(Ma, theta1=case.theta1)
+    ctx = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree, (case.k, 0, 0)), nx, N=N,
+                            precision=prec, bc_x=1)
+    taus = OA.model_taus(case.model)
+    P.lb_set_relaxation(ctx, taus, True, 1.0, left, right)
+    return olat, d, idx, case, h0, ctx, taus
+
+
+@pytest.mark.parametrize("name,N,prec", [("D3Q39", 3, "f64"), ("D3Q103", 4, "f64"), ("D3Q103", 4, "f32")])
+def test_step_adjoint_matches_oracle(name, N, prec):
+    olat, d, idx, case, h0, ctx, taus = _setup(name, N, 2.0, 150, prec)
+    rng = np.random.default_rng(9)
+    h = h0 * (1 + 0.03 * rng.standard_normal(h0.shape))
+    st = upload(ctx, h, idx)
+    if prec != "f64":
+        h = download(ctx, st, idx).reshape(h.shape)
+    lam_next = rng.standard_normal(h.shape)
+    want_lam, want_g = OA.step_vjp(h, lam_next, case.model, case.geom, taus)
+    ln = _plain_up(ctx, lam_next, idx)
+    lt = torch.full_like(ln, np.nan)
+    dtau = torch.zeros(len(taus), dtype=torch.float64, device="cuda")
+    P.lb_step_adjoint(ctx, st, ln, lt, dtau)
+    got = _plain_down(ctx, lt, idx)
+    assert np.isfinite(got).all()
+    scale = np.abs(want_lam).max()
+    assert np.abs(got - want_lam.reshape(olat.q, -1)).max() / scale < 1e-11
+    np.testing.assert_allclose(dtau.cpu().numpy(), want_g, rtol=1e-9, atol=1e-12 * np.abs(want_g).max())
+
+
+def test_step_adjoint_periodic_box_matches_oracle():
+    olat = OL.d3q39()
+    d = P.lb_lattice_named("D3Q39")
+    idx = lib_from_oracle(olat, d)
+    shape = (7, 8, 9)
+    rho, u, th = synthetic.taylor_green(0, amplitude=0.1, noise=1e-2, shape=shape)
+    f = OS.equilibrium(rho.ravel(), u.reshape(3, -1), th.ravel(), olat, 3)
+    rng = np.random.default_rng(3)
+    h = (f * (1 + 0.03 * rng.standard_normal(f.shape))).reshape(olat.q, *shape)
+    model = OS.Model(olat, 3, tau_ref=0.8)
+    geom = OS.Geometry(shape=shape, shift=(1, 0, 0))
+    taus = OA.model_taus(model)
+    ctx = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree, (1, 0, 0)), 9, 8, 7, N=3, precision="f64")
+    P.lb_set_relaxation(ctx, taus, True, 1.0)
+    lam_next = rng.standard_normal(h.shape)
+    want_lam, want_g = OA.step_vjp(h, lam_next, model, geom, taus)
+    lt = torch.zeros(ctx.state_elems, dtype=torch.float64, device="cuda")
+    dtau = torch.zeros(len(taus), dtype=torch.float64, device="cuda")
+    P.lb_step_adjoint(ctx, upload(ctx, h, idx), _plain_up(ctx, lam_next, idx), lt, dtau)
+    got = _plain_down(ctx, lt, idx)
+    assert np.abs(got - want_lam.reshape(olat.q, -1)).max() / np.abs(want_lam).max() < 1e-11
+    np.testing.assert_allclose(dtau.cpu().numpy(), want_g, rtol=1e-9, atol=1e-12 * np.abs(want_g).max())
+
+
+def test_moments_adjoint_matches_oracle():
+    olat, d, idx, case, h0, ctx, taus = _setup("D3Q103", 4, 2.0, 140, "f64")
+    rng = np.random.default_rng(2)
+    h = h0 * (1 + 0.02 * rng.standard_normal(h0.shape))
+    rho, th, q = OA.loss_moments(h, case.model, case.geom)
+    target = (rho * 1.01, th * 0.99, q + 0.01)
+    want = OA.shock_loss_grad(h, case.model, case.geom, target)
+    st = upload(ctx, h, idx)
+    mask = P.LB_MOM_RHO | P.LB_MOM_THETA | P.LB_MOM_Q
+    m = P.lb_moments(ctx, st, mask)                    # rows: rho, theta, qx, qy, qz
+    tgt = torch.from_numpy(np.stack(target)).cuda()
+    gbar = torch.zeros_like(m)
+    gbar[0] = 2 * (m[0] - tgt[0])
+    gbar[1] = 2 * (m[1] - tgt[1])
+    gbar[2] = 2 * (m[2] - tgt[2])
+    lam = torch.full((ctx.state_elems,), np.nan, dtype=torch.float64, device="cuda")
+    P.lb_moments_adjoint(ctx, st, gbar, mask, lam)
+    got = _plain_down(ctx, lam, idx)
+    assert np.abs(got - want.reshape(olat.q, -1)).max() / np.abs(want).max() < 1e-10
+
+
+def test_relaxation_run_gradient_matches_oracle():
+    """Checkpointed autograd run (24 steps, checkpoint every 10) vs the oracle's discrete adjoint."""
+    olat, d, idx, case, h0, ctx, taus = _setup("D3Q39", 3, 1.5, 40, "f64")
+    target_taus = taus * synthetic.perturbed(np.ones(len(taus)), 0.2, seed=7)
+    mt = OA.model_with_taus(case.model, target_taus)
+    h = h0
+    for _ in range(24):
+        h = OS.step(h, mt, case.geom)
+    target = OA.loss_moments(h, mt, case.geom)
+    Lwant, gwant, _ = OA.run_gradient(h0, case.model, case.geom, taus, 24, target, checkpoint_every=10)
+    tau = torch.tensor(taus, dtype=torch.float64, requires_grad=True)
+    out = relaxation_run(ctx, tau, upload(ctx, h0, idx), 24, checkpoint_every=10)
+    tgt = torch.from_numpy(np.stack(target)).cuda()
+    loss = ((out[0] - tgt[0]) ** 2 + (out[1] - tgt[1]) ** 2 + (out[2] - tgt[2]) ** 2).sum()
+    loss.backward()
+    assert abs(loss.item() - Lwant) < 1e-10 * Lwant
+    np.testing.assert_allclose(tau.grad.numpy(), gwant, rtol=1e-8, atol=1e-10 * np.abs(gwant).max())
+
+
+def test_differentiable_shock_ma5_full_size():
+    """Ma = 5, 1024 cells, D3Q103, N = 4, 5000 steps, checkpoint every 250; target = the oracle's
+    run at the Table 4 times; start = the six fitted times perturbed +-20 % by seed. The adjoint
+    gradient (FP64 forward) agrees with central differences (h = 1e-4 relative) to 1e-4, the
+    FP32-forward adjoint with the FP64 one to 1e-2, and d L / d tau_bulk vanishes."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "ma5_d3q103_n4_target.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden target not generated")
+    gold = np.load(path)
+    olat, d, idx, case, h0, ctx, taus_ref = _setup("D3Q103", 4, 5.0, 1024, "f64", width=10.0)
+    keys = OA.tau_keys(4)
+    fitted = [(2, 0), (3, 1), (3, 0), (4, 1), (4, 2), (2, 1)]
+    taus0 = taus_ref.copy()
+    pert = synthetic.perturbed(np.ones(len(fitted)), 0.2)
+    for k, p in zip(fitted, pert):
+        taus0[keys.index(k)] *= p
+    tgt = torch.from_numpy(np.stack([gold["rho_5000"], gold["theta_5000"], gold["q_5000"]])).cuda()
+
+    def loss_of(ctx_, tau_np, h0_state):
+        tau = torch.tensor(tau_np, dtype=torch.float64, requires_grad=True)
+        out = relaxation_run(ctx_, tau, h0_state, 5000, checkpoint_every=250)
+        L = ((out[0] - tgt[0]) ** 2 + (out[1] - tgt[1]) ** 2 + (out[2] - tgt[2]) ** 2).sum()
+        return L, tau
+
+    L, tau = loss_of(ctx, taus0, upload(ctx, h0, idx))
+    L.backward()
+    g = tau.grad.numpy()
+    assert P.lb_poll_status(ctx)[0] == 0
+    gmax = np.abs(g).max()
+    for k in fitted:
+        p = keys.index(k)
+        vals = []
+        for sgn in (1, -1):
+            t = taus0.copy()
+            t[p] += sgn * 1e-4 * taus0[p]
+            with torch.no_grad():
+                Lp, _ = loss_of(ctx, t, upload(ctx, h0, idx))
+            vals.append(Lp.item())
+        fd = (vals[0] - vals[1]) / (2e-4 * taus0[p])
+        assert abs(fd - g[p]) <= 1e-4 * abs(fd) + 1e-7 * gmax, (k, fd, g[p])
+    assert abs(g[keys.index((2, 1))]) < 1e-6 * gmax
+    # FP32 forward, FP64 adjoint arithmetic
+    _, _, _, _, _, ctx32, _ = _setup("D3Q103", 4, 5.0, 1024, "f32", width=10.0)
+    L32, tau32 = loss_of(ctx32, taus0, upload(ctx32, h0, idx))
+    L32.backward()
+    np.testing.assert_allclose(tau32.grad.numpy(), g, rtol=1e-2, atol=1e-3 * gmax)
