@@ -175,6 +175,21 @@ lb_status lb_moments(lb_ctx *ctx, const void *f, double *out, unsigned which_mas
 lb_status lb_step_adjoint(lb_ctx *ctx, const void *f_t, const double *lam_next, double *lam_t,
                           double *dtau);
 
+/* lb_step_adjoint_noalloc -- lb_step_adjoint for callers that may not allocate device memory
+ * when they run it: work captured into a CUDA graph (cudaMalloc cannot be captured), code
+ * whose device memory all belongs to its own pool allocator, or a process with a fixed
+ * device-memory budget. The paper has no counterpart; the arguments, results and errors are
+ * those of lb_step_adjoint, and the call allocates nothing. Instead of the context's scratch
+ * it uses one fixed array of 8192 x 10 doubles (640 KB) that every GPU loading libsmrt holds
+ * until the process exits, enough for grids of up to 8192 blocks of 128 cells (1,048,576
+ * cells); larger grids return LB_ERR_INVALID. The first call on a device looks up that
+ * array's device address: make that first call before any stream capture. All calls share
+ * the array and it keeps the last call's partial sums (each call overwrites the slots it reads,
+ * so nothing needs clearing), hence calls that may overlap on the GPU -- on different streams
+ * or contexts of one device -- race and must be ordered by the caller. */
+lb_status lb_step_adjoint_noalloc(lb_ctx *ctx, const void *f_t, const double *lam_next,
+                                  double *lam_t, double *dtau);
+
 /* lb_moments_adjoint -- reverse mode of lb_moments for the row groups LB_MOM_RHO, LB_MOM_U,
  * LB_MOM_THETA and LB_MOM_Q: given gbar = dL/d(moments) in lb_moments' layout for which_mask
  * (rows x lb_cells doubles, device), writes lam = dL/df (device doubles, state layout,

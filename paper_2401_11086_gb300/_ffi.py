@@ -38,6 +38,7 @@ SIGNATURES = {
     "lb_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_uint]),
     "lb_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lb_moments_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
+    "lb_step_adjoint_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lb_poll_status": (c_int, [c_void_p, POINTER(c_uint)]),
     "lb_cells": (c_size_t, [c_void_p]),
     "lb_plane_stride": (c_size_t, [c_void_p]),

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -412,4 +413,53 @@ extern "C" void lb_destroy(lb_ctx *c) {
     cudaStreamSynchronize(c->view.stream);
     free_tables(c);
     delete c;
+}
+
+// ----------------------------------------------------------------------------------------
+// lb_step_adjoint_noalloc: lb_step_adjoint for callers that cannot allocate device memory at
+// the time they step backwards (code running under CUDA stream capture, where cudaMalloc is
+// not allowed; frameworks whose own pool allocator owns all device memory; hosts with a hard
+// device-memory budget). The per-block gradient partials live in the fixed-size device array
+// below instead of the context's scratch. It is reserved once per process on every GPU that
+// loads libsmrt and kept until exit; every call on every context of that GPU shares it.
+namespace {
+
+constexpr long long kNoallocMaxBlocks = 8192;  // 8192 blocks of 128 cells = 1,048,576 cells
+__device__ __align__(256) double g_noalloc_partials[kNoallocMaxBlocks * kMaxTau];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// The device address of g_noalloc_partials on the current device, looked up on first use
+// (in host code the array's name is only a stand-in; kernels need the device address).
+lb_status noalloc_scratch(double **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return LB_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return LB_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_step_adjoint_noalloc(lb_ctx *c, const void *f_t, const double *lam_next, double *lam_t,
+                                             double *dtau) {
+    if (!c || !f_t || !lam_next || !lam_t || !dtau || lam_next == lam_t) return LB_ERR_INVALID;
+    if (!c->as) return LB_ERR_UNSUPPORTED;
+    if (!c->relax_set) return LB_ERR_INVALID;
+    const size_t bytes = sizeof(double) * lb_state_elems(c);
+    const char *a0 = reinterpret_cast<const char *>(lam_next), *b0 = reinterpret_cast<const char *>(lam_t);
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;
+    if (adj_blocks(c->view) > kNoallocMaxBlocks) return LB_ERR_INVALID;  // grid too large
+    double *scratch = nullptr;
+    const lb_status st = noalloc_scratch(&scratch);
+    if (st != LB_OK) return st;
+    // every block writes its own slot before the reduction reads it: nothing to clear
+    return cuda_status(c->as->step(c->view, f_t, lam_next, lam_t, scratch, dtau));
 }
