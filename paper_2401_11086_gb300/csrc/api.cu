@@ -44,6 +44,7 @@ struct lb_ctx {
     InstanceInfo *d_inst;
     int2 *d_tiles;
     void *d_ghosts;
+    double *d_ghostsd;
     double *d_states;
     unsigned *d_health;
     double *d_partials;  // per-block relaxation-time gradients of lb_step_adjoint
@@ -91,6 +92,7 @@ void free_tables(lb_ctx *c) {
     cudaFree(c->d_inst);
     cudaFree(c->d_tiles);
     cudaFree(c->d_ghosts);
+    cudaFree(c->d_ghostsd);
     cudaFree(c->d_states);
     cudaFree(c->d_health);
     cudaFree(c->d_partials);
@@ -226,6 +228,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     e = cudaMalloc(&c->d_inst, sizeof(InstanceInfo) * grid->batch);
     if (e == cudaSuccess && !tiles.empty()) e = cudaMalloc(&c->d_tiles, sizeof(int2) * tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghosts, c->elem * c->q * 2 * grid->batch);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ghostsd, sizeof(double) * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_states, sizeof(double) * 10 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_health, 16);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * kMaxTau * std::max(1LL, adj_blocks(v)));
@@ -239,6 +242,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_health, 0, 16, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ghosts, 0, c->elem * c->q * 2 * grid->batch, v.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ghostsd, 0, sizeof(double) * c->q * 2 * grid->batch, v.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * grid->batch,
                             cudaMemcpyHostToDevice, v.stream);
@@ -251,6 +255,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     v.inst = c->d_inst;
     v.tiles = c->d_tiles;
     v.ghosts = c->d_ghosts;
+    v.ghostsd = c->d_ghostsd;
     v.health = c->d_health;
     c->relax_set = false;
     *out = c;
@@ -302,7 +307,7 @@ extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell
     if (e == cudaSuccess && c->view.fixedx) {
         e = cudaMemcpyAsync(c->d_states, c->h_states.data(), sizeof(double) * 10 * c->batch,
                             cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = c->ks->ghost(c->view, c->d_states, c->batch, c->d_ghosts);
+        if (e == cudaSuccess) e = c->ks->ghost(c->view, c->d_states, c->batch, c->d_ghosts, c->d_ghostsd);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables are reused next call
     if (e != cudaSuccess) return LB_ERR_CUDA;
@@ -336,6 +341,7 @@ extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;  // overlap
     void *src = fa, *dst = fb;
     for (int s = 0; s < nsteps; ++s) {
+        c->view.step++;
         const cudaError_t e = c->ks->step(c->view, src, dst);
         if (e != cudaSuccess) return LB_ERR_CUDA;
         std::swap(src, dst);

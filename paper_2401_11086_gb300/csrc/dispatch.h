@@ -26,15 +26,18 @@ struct CtxView {
     const int2 *tiles;
     int ntiles;
     const void *ghosts;
+    const double *ghostsd;  // end-state deviations in double
     unsigned *health;
     long long ncells;
+    unsigned step;  // launch counter of lb_step (seeds the stochastic rounding)
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
 using MomentsFn = cudaError_t (*)(const CtxView &, const void *f, double *out, unsigned mask);
 using FillFn = cudaError_t (*)(const CtxView &, void *f, const double *rho, const double *u,
                                const double *theta);
-using GhostFn = cudaError_t (*)(const CtxView &, const double *states, int ninst, void *ghosts);
+using GhostFn = cudaError_t (*)(const CtxView &, const double *states, int ninst, void *ghosts,
+                                double *ghostsd);
 
 struct KernelSet {
     StepFn step;
@@ -55,16 +58,22 @@ StepArgs<Lat, T> make_args(const CtxView &v, const void *fin, void *fout) {
     a.inst = v.inst;
     a.tiles = v.tiles;
     a.ghosts = static_cast<const T *>(v.ghosts);
+    a.ghostsd = v.ghostsd;
     a.health = v.health;
     for (int i = 0; i < Lat::Q; ++i) a.plane[i] = v.plane[i];
-    for (int p = 0; p <= Lat::NP; ++p) a.wp[p] = T(v.wp[p]);
+    for (int p = 0; p <= Lat::NP; ++p) {
+        a.wp[p] = T(v.wp[p]);
+        a.wpd[p] = v.wp[p];
+    }
     a.c = T(v.c);
+    a.cd = v.c;
     a.nx = v.nx;
     a.ny = v.ny;
     a.nz = v.nz;
     a.kx = v.kx;
     a.ky = v.ky;
     a.kz = v.kz;
+    a.step = v.step;
     return a;
 }
 
@@ -115,10 +124,11 @@ cudaError_t launch_fill(const CtxView &v, void *f, const double *rho, const doub
 }
 
 template <class Lat, int N, class T>
-cudaError_t launch_ghost(const CtxView &v, const double *states, int ninst, void *ghosts) {
+cudaError_t launch_ghost(const CtxView &v, const double *states, int ninst, void *ghosts, double *ghostsd) {
     const StepArgs<Lat, T> a = make_args<Lat, T>(v, nullptr, nullptr);
     const int n = 2 * ninst;
-    ghost_kernel<Lat, N, T><<<(n + 63) / 64, 64, 0, v.stream>>>(a, states, ninst, static_cast<T *>(ghosts));
+    ghost_kernel<Lat, N, T><<<(n + 63) / 64, 64, 0, v.stream>>>(a, states, ninst, static_cast<T *>(ghosts),
+                                                                 ghostsd);
     return cudaGetLastError();
 }
 

@@ -61,13 +61,38 @@ struct StepArgs {
     const InstanceInfo *__restrict__ inst;
     const int2 *__restrict__ tiles;  // line kernel: (instance, first x) per block
     const T *__restrict__ ghosts;    // [instance][2][Q], library order
+    const double *__restrict__ ghostsd;  // the same end-state deviations in double
     unsigned *health;
     long long plane[Lat::Q];  // element offset of each population plane, library order
     T wp[Lat::NP + 1];        // weight of the rest velocity, then of each pair
+    double wpd[Lat::NP + 1];  // the same weights in double, for every double-precision rebuild
     T c;
+    double cd;                // c in double
     int nx, ny, nz;           // box kernel geometry
     int kx, ky, kz;           // box kernel frame shift
+    unsigned step;            // step counter (stochastic rounding of the split precision)
 };
+
+// Stochastic rounding of a double to float: round to the float neighbour above or below with
+// probabilities proportional to the distances, drawn from a counter-based hash of
+// (cell, population, step), so that storing a steady state leaves no systematic bias.
+SMRT_D unsigned mix32(unsigned h) {  // the 32-bit finaliser of MurmurHash3
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+SMRT_D float round_stochastic(double x, unsigned key) {
+    const float xf = __double2float_rn(x);
+    const double r = x - double(xf);
+    if (r == 0.0) return xf;
+    const float xn = nextafterf(xf, r > 0.0 ? INFINITY : -INFINITY);
+    const double gap = fabs(double(xn) - double(xf));
+    const double u = double(mix32(key) >> 8) * (1.0 / 16777216.0);
+    return (u * gap < fabs(r)) ? xn : xf;
+}
 
 template <class T>
 SMRT_D T rcp_tau(T A, T B, T rho) {
@@ -88,20 +113,34 @@ struct Collide {
     //   theta - 1 = (E - 3 - 3 (rho - 1) - rho |u|^2) / (3 rho),
     // which keeps rho - 1 and theta - 1 free of cancellation.
     SMRT_D static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
-                                  Acc &theta, Acc &thm1) {
-        Acc r = Acc(f[0]), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
+                                 Acc &theta, Acc &thm1) {
+        Acc raw[5];
+        conserved(f, c, rho, rhom1, u, theta, thm1, raw);
+    }
+    // ... also returning the raw sums (sum df, sum e df, sum |e|^2 df) in raw[0..4]
+    SMRT_D static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
+                                 Acc &theta, Acc &thm1, Acc (&raw)[5], const Acc *res = nullptr) {
+        // res (optional): what the stored float values lack against their exact values
+        // (end-state populations pulled from beyond a fixed end, kept in double)
+        auto val = [&](int i) { return res ? Acc(f[i]) + res[i] : Acc(f[i]); };
+        Acc r = val(0), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
         static_for<NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
             constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
             constexpr int ee = e0 * e0 + e1 * e1 + e2 * e2;
-            const Acc sp = Acc(f[2 * p + 1]) + Acc(f[2 * p + 2]);
-            const Acc dp = Acc(f[2 * p + 1]) - Acc(f[2 * p + 2]);
+            const Acc sp = val(2 * p + 1) + val(2 * p + 2);
+            const Acc dp = val(2 * p + 1) - val(2 * p + 2);
             r += sp;
             if constexpr (e0 != 0) j0 = fma(Acc(e0), dp, j0);
             if constexpr (e1 != 0) j1 = fma(Acc(e1), dp, j1);
             if constexpr (e2 != 0) j2 = fma(Acc(e2), dp, j2);
             en = fma(Acc(ee), sp, en);
         });
+        raw[0] = r;
+        raw[1] = j0;
+        raw[2] = j1;
+        raw[3] = j2;
+        raw[4] = en;
         rhom1 = r;
         rho = Acc(1) + r;
         const Acc ir = rcp(rho);
@@ -183,8 +222,8 @@ struct Collide {
 
     // a7 + a8 helper: values f'_i = w_i sum_gamma P_gamma e_i^gamma with
     // P_gamma = c^|gamma| sum_alpha hfull(alpha, gamma) ta'_alpha; U is the arithmetic type.
-    template <class U>
-    SMRT_D static void rebuild(const U (&ta)[M], U c, const T (&wp)[NP + 1], U (&out)[Q]) {
+    template <class U, class W>
+    SMRT_D static void rebuild(const U (&ta)[M], U c, const W (&wp)[NP + 1], U (&out)[Q]) {
         U cp[N + 1];
         cp[0] = U(1);
         static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
@@ -238,12 +277,13 @@ struct Collide {
 
     // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
     // Returns false when rho or theta is not positive (or NaN).
-    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], T c, const T *tauA,
-                               const T *tauB) {
+    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const double (&wpd)[NP + 1], T c,
+                               double cd, const T *tauA, const T *tauB, unsigned key = 0u,
+                               const Acc *res = nullptr) {
         // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
         T v[M], Rc[M];
         absolute<N>(f, c, v, Rc);
-        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a;
+        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a, raw_a[5];
         if constexpr (std::is_same<Acc, T>::value) {
             // a2 from the raw moments already formed: rho - 1 = Rc_0, rho u = Rc_1,
             // E - 3 = tr Rc_2
@@ -258,12 +298,32 @@ struct Collide {
             thm1_a = (em3 - T(3) * rhom1_a - rho_a * uu) * ir * T(1.0 / 3.0);
             th_a = T(1) + thm1_a;
         } else {
-            conserved(f, Acc(c), rho_a, rhom1_a, u_a, th_a, thm1_a);
+            conserved(f, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a, raw_a, res);
         }
         const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
         const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
         const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
-        v[0] = rho;
+        if constexpr (Split) {
+            // absolute coefficients in Acc, minus the Acc equilibrium: the float transforms
+            // below then act on the small non-equilibrium remainder only (d^eq = (rho, 0, ...)
+            // in the local frame, so d_n = [T^-1 (a - a^eq)]_n for n >= 2)
+            using CA = Collide<Lat, N, Acc, Acc, false>;
+            Acc fa[Q], va[M], Ra[M], teq[M];
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                fa[i] = res ? Acc(f[i]) + res[i] : Acc(f[i]);
+            });
+            CA::template absolute<N>(fa, Acc(cd), va, Ra);
+            equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
+            teq[0] = rho_a;
+            va[0] = rho_a;
+            static_for<M>([&](auto A) {
+                constexpr int p = decltype(A)::value;
+                v[p] = T(va[p] - teq[p]);
+            });
+        } else {
+            v[0] = rho;
+        }
         to_local<N>(v, u, theta, thm1);
 
         // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u
@@ -304,13 +364,46 @@ struct Collide {
             // equilibrium part in Acc from the Acc moments, non-equilibrium part in T
             Acc teq[M];
             equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
-            Acc oeq[Q];
-            rebuild<Acc>(teq, Acc(c), wp, oeq);
+            // the equilibrium part takes the weights in double: float-rounded weights would
+            // bias the conserved moments of every cell by ~1e-8 per step
+            Acc out[Q];
+            rebuild<Acc>(teq, Acc(cd), wpd, out);
             T oneq[Q];
             rebuild<T>(v, c, wp, oneq);
+            static_for<Q>([&](auto I) { out[decltype(I)::value] += Acc(oneq[decltype(I)::value]); });
+            // Conservation in Acc: float arithmetic in the non-equilibrium part leaves errors
+            // that freeze once the flow is steady and would drift rho, rho u and E. Restore the
+            // pre-collision sums exactly along the conserved directions
+            //   d_i = w_i (A + B.e_i + C (|e_i|^2 - 3/c^2)),
+            // using sum w = 1, sum w e e = 1/c^2, sum w |e|^2 = 3/c^2, sum w |e|^4 = 15/c^4.
+            Acc m0 = out[0], m1 = Acc(0), m2 = Acc(0), m3 = Acc(0), m4 = Acc(0);
+            static_for<NP>([&](auto P) {
+                constexpr int p = decltype(P)::value;
+                constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
+                const Acc sp = out[2 * p + 1] + out[2 * p + 2], dp = out[2 * p + 1] - out[2 * p + 2];
+                m0 += sp;
+                if constexpr (e0 != 0) m1 = fma(Acc(e0), dp, m1);
+                if constexpr (e1 != 0) m2 = fma(Acc(e1), dp, m2);
+                if constexpr (e2 != 0) m3 = fma(Acc(e2), dp, m3);
+                m4 = fma(Acc(e0 * e0 + e1 * e1 + e2 * e2), sp, m4);
+            });
+            const Acc c2 = Acc(cd) * Acc(cd);
+            const Acc A = raw_a[0] - m0;
+            const Acc B0 = c2 * (raw_a[1] - m1), B1 = c2 * (raw_a[2] - m2), B2 = c2 * (raw_a[3] - m3);
+            const Acc C = c2 * c2 * (raw_a[4] - m4 - Acc(3) * A / c2) / Acc(6);
+            const Acc base = A - C * Acc(3) / c2;
+            out[0] += Acc(wpd[0]) * base;
+            static_for<NP>([&](auto P) {
+                constexpr int p = decltype(P)::value;
+                constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
+                const Acc ev = base + C * Acc(e0 * e0 + e1 * e1 + e2 * e2);
+                const Acc od = B0 * Acc(e0) + B1 * Acc(e1) + B2 * Acc(e2);
+                out[2 * p + 1] += Acc(wpd[p + 1]) * (ev + od);
+                out[2 * p + 2] += Acc(wpd[p + 1]) * (ev - od);
+            });
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                f[i] = T(oeq[i] + Acc(oneq[i]));
+                f[i] = round_stochastic(out[i], key ^ (0x9e3779b9u * (i + 1)));
             });
         }
         return ok;
@@ -342,7 +435,8 @@ __global__ void __launch_bounds__(128) step_box_kernel(StepArgs<Lat, T> a) {
             f[i] = a.fin[a.plane[i] + zs * slab + ys * row + xs];
         });
     });
-    const bool ok = C::collide(f, a.wp, a.c, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]));
+    const bool ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]),
+                               mix32(unsigned(z * slab + y * row + x) ^ mix32(a.step)));
     if (!ok) atomicOr(a.health, 1u);
     const long long cell = z * slab + y * row + x;
     static_for<Lat::Q>([&](auto I) {
@@ -364,13 +458,27 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
     const long long base = in.cell_off;
     const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
     const T *gr = gl + Lat::Q;
+    const double *gld = a.ghostsd + (long long)tile.x * 2 * Lat::Q;
+    const double *grd = gld + Lat::Q;
+    constexpr bool Res = Split && FixedX;  // keep the float end states' rounding residuals
+    Acc res[Lat::Q];
+    if constexpr (Res) static_for<Lat::Q>([&](auto I) { res[decltype(I)::value] = Acc(0); });
     T f[Lat::Q];
     {  // the rest population streams by k as well
         const int xs = x - in.kx;
-        if constexpr (FixedX)
-            f[0] = xs < 0 ? gl[0] : (xs >= L ? gr[0] : a.fin[a.plane[0] + base + xs]);
-        else
+        if constexpr (FixedX) {
+            if (xs < 0) {
+                f[0] = gl[0];
+                if constexpr (Res) res[0] = Acc(gld[0]) - Acc(gl[0]);
+            } else if (xs >= L) {
+                f[0] = gr[0];
+                if constexpr (Res) res[0] = Acc(grd[0]) - Acc(gr[0]);
+            } else {
+                f[0] = a.fin[a.plane[0] + base + xs];
+            }
+        } else {
             f[0] = a.fin[a.plane[0] + base + wrap(xs, L)];
+        }
     }
     static_for<Lat::NP>([&](auto P) {
         constexpr int p = decltype(P)::value;
@@ -379,18 +487,22 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
             constexpr int i = 2 * p + 1 + decltype(Sg)::value;
             const int xs = x - (sg * Lat::e(p, 0) + in.kx);
             if constexpr (FixedX) {
-                if (xs < 0)
+                if (xs < 0) {
                     f[i] = gl[i];
-                else if (xs >= L)
+                    if constexpr (Res) res[i] = Acc(gld[i]) - Acc(gl[i]);
+                } else if (xs >= L) {
                     f[i] = gr[i];
-                else
+                    if constexpr (Res) res[i] = Acc(grd[i]) - Acc(gr[i]);
+                } else {
                     f[i] = a.fin[a.plane[i] + base + xs];
+                }
             } else {
                 f[i] = a.fin[a.plane[i] + base + wrap(xs, L)];
             }
         });
     });
-    const bool ok = C::collide(f, a.wp, a.c, tau_a<T>(in), tau_b<T>(in));
+    const bool ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
+                               mix32(unsigned(base + x) ^ mix32(a.step)), Res ? res : nullptr);
     if (!ok) atomicOr(a.health, 1u);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -427,7 +539,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
         const int L = in.nx;
         if (x >= L) return;
         cell = in.cell_off + x;
-        ubar_x = double(a.c) * in.kx;
+        ubar_x = a.cd * in.kx;
         const T *gl = a.ghosts + (long long)tile.x * 2 * Lat::Q;
         const T *gr = gl + Lat::Q;
         {
@@ -459,7 +571,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
         if (x >= a.nx) return;
         const long long row = a.nx, slab = row * a.ny;
         cell = z * slab + y * row + x;
-        ubar_x = double(a.c) * a.kx;
+        ubar_x = a.cd * a.kx;
         f[0] = a.fin[a.plane[0] + wrap(z - a.kz, a.nz) * slab + wrap(y - a.ky, a.ny) * row + wrap(x - a.kx, a.nx)];
         static_for<Lat::NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
@@ -474,7 +586,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
         });
     }
     Acc rho, rhom1, u[3], th, thm1;
-    C::conserved(f, Acc(a.c), rho, rhom1, u, th, thm1);
+    C::conserved(f, Acc(a.cd), rho, rhom1, u, th, thm1);
     T v[Mm];
     Cm::template absolute<Nm>(f, a.c, v);
     v[0] = T(rho);
@@ -494,8 +606,8 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
     if (m.mask & 0x1u) o[(r++) * nc + cell] = double(rho);
     if (m.mask & 0x2u) {
         o[(r++) * nc + cell] = double(u[0]) + ubar_x;
-        o[(r++) * nc + cell] = double(u[1]) + double(a.c) * a.ky;
-        o[(r++) * nc + cell] = double(u[2]) + double(a.c) * a.kz;
+        o[(r++) * nc + cell] = double(u[1]) + a.cd * a.ky;
+        o[(r++) * nc + cell] = double(u[2]) + a.cd * a.kz;
     }
     if (m.mask & 0x4u) o[(r++) * nc + cell] = thd;
     if (m.mask & 0x8u) {
@@ -524,7 +636,7 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
 // df = order-N equilibrium of (rho, u_phys - u_bar, theta) minus w_i, in double, stored as T.
 template <class Lat, int N, class T>
 SMRT_D void equilibrium_cell(double rho, const double (&u)[3], double theta, double c,
-                              const T (&wp)[Lat::NP + 1], double (&out)[Lat::Q]) {
+                             const double (&wp)[Lat::NP + 1], double (&out)[Lat::Q]) {
     using C = Collide<Lat, N, T, double, false>;
     double ta[nmom(N)];
     C::template equilibrium<double>(rho, rho - 1.0, u, theta - 1.0, ta);
@@ -549,10 +661,10 @@ __global__ void __launch_bounds__(128) fill_kernel(StepArgs<Lat, T> a, const dou
         if (cell >= ncells) return;
         kx = a.kx;
     }
-    const double uu[3] = {u[cell] - double(a.c) * kx, u[ncells + cell] - double(a.c) * a.ky,
-                          u[2 * ncells + cell] - double(a.c) * a.kz};
+    const double uu[3] = {u[cell] - a.cd * kx, u[ncells + cell] - a.cd * a.ky,
+                          u[2 * ncells + cell] - a.cd * a.kz};
     double out[Lat::Q];
-    equilibrium_cell<Lat, N, T>(rho[cell], uu, theta[cell], double(a.c), a.wp, out);
+    equilibrium_cell<Lat, N, T>(rho[cell], uu, theta[cell], a.cd, a.wpd, out);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         a.fout[a.plane[i] + cell] = T(out[i]);
@@ -561,18 +673,20 @@ __global__ void __launch_bounds__(128) fill_kernel(StepArgs<Lat, T> a, const dou
 
 // End-state populations of instance j: states[j] = (rho, u_phys, theta) left then right.
 template <class Lat, int N, class T>
-__global__ void ghost_kernel(StepArgs<Lat, T> a, const double *states, int ninst, T *ghosts) {
+__global__ void ghost_kernel(StepArgs<Lat, T> a, const double *states, int ninst, T *ghosts,
+                             double *ghostsd) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * ninst) return;
     const int j = t / 2;
     const double *s = states + 5 * t;
-    const double ub = double(a.c) * a.inst[j].kx;
-    const double uu[3] = {s[1] - ub, s[2] - double(a.c) * a.ky, s[3] - double(a.c) * a.kz};
+    const double ub = a.cd * a.inst[j].kx;
+    const double uu[3] = {s[1] - ub, s[2] - a.cd * a.ky, s[3] - a.cd * a.kz};
     double out[Lat::Q];
-    equilibrium_cell<Lat, N, T>(s[0], uu, s[4], double(a.c), a.wp, out);
+    equilibrium_cell<Lat, N, T>(s[0], uu, s[4], a.cd, a.wpd, out);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         ghosts[(long long)t * Lat::Q + i] = T(out[i]);
+        ghostsd[(long long)t * Lat::Q + i] = out[i];
     });
 }
 

@@ -145,7 +145,8 @@ def test_differentiable_shock_ma5_full_size():
     """Ma = 5, 1024 cells, D3Q103, N = 4, 5000 steps, checkpoint every 250; target = the oracle's
     run at the Table 4 times; start = the six fitted times perturbed +-20 % by seed. The adjoint
     gradient (FP64 forward) agrees with central differences (h = 1e-4 relative) to 1e-4, the
-    FP32-forward adjoint with the FP64 one to 1e-2, and d L / d tau_bulk vanishes."""
+    adjoint of the FP32 forward run (FP64 conserved sums and equilibrium) with the FP64 one to
+    5e-3, and d L / d tau_bulk vanishes."""
     path = os.path.join(os.path.dirname(__file__), "golden", "ma5_d3q103_n4_target.npz")
     if not os.path.exists(path):
         pytest.skip("golden target not generated")
@@ -183,7 +184,7 @@ def test_differentiable_shock_ma5_full_size():
         assert abs(fd - g[p]) <= 1e-4 * abs(fd) + 1e-7 * gmax, (k, fd, g[p])
     assert abs(g[keys.index((2, 1))]) < 1e-6 * gmax
     # FP32 forward, FP64 adjoint arithmetic
-    _, _, _, _, _, ctx32, _ = _setup("D3Q103", 4, 5.0, 1024, "f32", width=10.0)
+    _, _, _, _, _, ctx32, _ = _setup("D3Q103", 4, 5.0, 1024, "f32c64", width=10.0)
     L32, tau32 = loss_of(ctx32, taus0, upload(ctx32, h0, idx))
     L32.backward()
-    np.testing.assert_allclose(tau32.grad.numpy(), g, rtol=1e-2, atol=1e-3 * gmax)
+    np.testing.assert_allclose(tau32.grad.numpy(), g, rtol=5e-3, atol=1e-4 * gmax)
