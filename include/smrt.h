@@ -142,6 +142,43 @@ lb_status lb_fill_equilibrium(lb_ctx *ctx, void *f, const double *rho, const dou
  * Errors: LB_ERR_INVALID (null, nsteps < 1, relaxation unset), LB_ERR_CUDA. */
 lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 
+/* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128);
+ * persistent = 1: lb_step runs all its steps in one cooperative launch of blocks_per_sm
+ * blocks per SM (0 = as many as fit), tiles spread over the blocks, a grid-wide barrier between
+ * steps (its wait is bounded: on timeout the health word gets LB_HEALTH_TIMEOUT and the
+ * launch ends); persistent = 0: one launch per step. ms_per_step: measured by lb_autotune. */
+typedef struct {
+    int tile_width;
+    int blocks_per_sm;
+    int persistent;
+    double ms_per_step;
+} lb_schedule;
+
+/* lb_set_schedule / lb_get_schedule -- apply or read a schedule (a periodic box accepts only
+ * {128, 0, 0}). Setting a new tile width rebuilds the context's tile table (synchronises).
+ * Errors: LB_ERR_INVALID, LB_ERR_UNSUPPORTED (persistent kernel cannot be resident), LB_ERR_CUDA. */
+lb_status lb_set_schedule(lb_ctx *ctx, const lb_schedule *schedule);
+lb_status lb_get_schedule(const lb_ctx *ctx, lb_schedule *schedule);
+
+/* lb_autotune -- time every candidate schedule (tile widths 32/64/128, one launch per step or
+ * persistent with 1, 2, 4 or all resident blocks per SM) for trial_steps steps on the states
+ * f_a / f_b (which it ADVANCES: pass copies), apply the fastest and return it in *best with
+ * its ms_per_step. Synchronises. Errors: as lb_step, LB_ERR_CUDA. */
+lb_status lb_autotune(lb_ctx *ctx, void *f_a, void *f_b, int trial_steps, lb_schedule *best);
+
+/* lb_step_graph -- lb_step of a 1D-line context as a replay of a CUDA graph holding one
+ * persistent launch of nsteps steps (captured on first use for this (f_a, f_b, nsteps,
+ * schedule) and cached in the context; capture needs no allocation of device memory). Same
+ * buffer convention as lb_step. Errors: as lb_step, LB_ERR_UNSUPPORTED (box), LB_ERR_CUDA. */
+lb_status lb_step_graph(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
+
+/* lb_test_barrier_timeout -- failure-detection test of the persistent launch: runs two steps
+ * with the barrier's arrival count preset so that the barrier can never complete. Every block
+ * waits out its bounded spin (about a second), sets LB_HEALTH_TIMEOUT and returns; the next
+ * lb_poll_status reports LB_ERR_TIMEOUT and the context stays usable. f_a/f_b contents are
+ * undefined afterwards. Synchronises. Errors: as lb_step, LB_ERR_UNSUPPORTED (box). */
+lb_status lb_test_barrier_timeout(lb_ctx *ctx, void *f_a, void *f_b);
+
 /* Row groups of lb_moments' output, selected by which_mask. */
 #define LB_MOM_RHO 0x1u   /* 1 row:  rho                                                    */
 #define LB_MOM_U 0x2u     /* 3 rows: physical velocity u_x, u_y, u_z                        */
@@ -222,6 +259,13 @@ lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w_out, doubl
  * upstream rho1 and theta1; velocities in the shock frame, along +x (host memory out). */
 lb_status lb_rankine_hugoniot(double Ma, double gamma, double rho1, double theta1,
                               lb_state *left, lb_state *right);
+
+/* lb_shock_frame -- reference temperature and frame shift of a normal shock (Sec. 4.1-4.2):
+ * *theta1 = 1 when the downstream temperature stays below 2 (Ma <= 1.9), else the upstream
+ * temperature that puts the downstream one at theta2_max (< 2, the Hermite convergence bound);
+ * *kx = round(((u1 + u2)/2) / c), the integer shift minimising the largest relative speed.
+ * Host memory out. Errors: LB_ERR_INVALID. */
+lb_status lb_shock_frame(double Ma, double gamma, double c, double theta2_max, double *theta1, int *kx);
 
 const char *lb_error_string(lb_status status);
 void lb_destroy(lb_ctx *ctx);

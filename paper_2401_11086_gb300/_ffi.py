@@ -28,6 +28,11 @@ class LbState(ctypes.Structure):
     _fields_ = [("rho", c_double), ("u", c_double * 3), ("theta", c_double)]
 
 
+class LbSchedule(ctypes.Structure):
+    _fields_ = [("tile_width", c_int), ("blocks_per_sm", c_int), ("persistent", c_int),
+                ("ms_per_step", c_double)]
+
+
 # name -> (restype, argtypes); every symbol include/smrt.h declares
 SIGNATURES = {
     "lb_init_lattice": (c_int, [POINTER(c_void_p), POINTER(LbLatticeDesc), POINTER(LbGridDesc), c_int, c_int, c_void_p]),
@@ -40,12 +45,18 @@ SIGNATURES = {
     "lb_moments_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_uint, c_void_p]),
     "lb_step_adjoint_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lb_poll_status": (c_int, [c_void_p, POINTER(c_uint)]),
+    "lb_set_schedule": (c_int, [c_void_p, POINTER(LbSchedule)]),
+    "lb_get_schedule": (c_int, [c_void_p, POINTER(LbSchedule)]),
+    "lb_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, POINTER(LbSchedule)]),
+    "lb_step_graph": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "lb_test_barrier_timeout": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lb_cells": (c_size_t, [c_void_p]),
     "lb_plane_stride": (c_size_t, [c_void_p]),
     "lb_state_elems": (c_size_t, [c_void_p]),
     "lb_num_moment_rows": (c_int, [c_void_p, c_uint]),
     "lb_lattice_named": (c_int, [c_char_p, POINTER(c_int8), POINTER(c_double), POINTER(c_double), POINTER(c_int), POINTER(c_int), c_int]),
     "lb_rankine_hugoniot": (c_int, [c_double, c_double, c_double, c_double, POINTER(LbState), POINTER(LbState)]),
+    "lb_shock_frame": (c_int, [c_double, c_double, c_double, c_double, POINTER(c_double), POINTER(c_int)]),
     "lb_error_string": (c_char_p, [c_int]),
     "lb_destroy": (None, [c_void_p]),
 }

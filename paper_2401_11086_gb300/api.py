@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import (LB_F32, LB_F32_CONS64, LB_F64, LB_MOM_D, LB_MOM_Q, LB_MOM_RHO, LB_MOM_SIGMA,  # noqa: F401
-                   LB_MOM_THETA, LB_MOM_U, LbGridDesc, LbLatticeDesc, LbState)
+                   LB_MOM_THETA, LB_MOM_U, LbGridDesc, LbLatticeDesc, LbSchedule, LbState)
 
 PRECISIONS = {"f64": LB_F64, "f32": LB_F32, "f32c64": LB_F32_CONS64}
 
@@ -64,6 +64,13 @@ def lb_rankine_hugoniot(Ma: float, gamma: float = 5.0 / 3.0, rho1: float = 1.0, 
            "lb_rankine_hugoniot")
     as_dict = lambda s: {"rho": s.rho, "u": (s.u[0], s.u[1], s.u[2]), "theta": s.theta}  # noqa: E731
     return as_dict(left), as_dict(right)
+
+
+def lb_shock_frame(Ma: float, c: float, gamma: float = 5.0 / 3.0, theta2_max: float = 1.2):
+    """(theta1, kx): reference temperature and frame shift of a normal shock."""
+    t1, k = c_double(), c_int()
+    _check(_ffi.lib().lb_shock_frame(Ma, gamma, c, theta2_max, byref(t1), byref(k)), "lb_shock_frame")
+    return t1.value, k.value
 
 
 def lb_error_string(status: int) -> str:
@@ -219,6 +226,41 @@ def lb_moments_adjoint(ctx: Context, f, gbar, mask: int, lam):
     _check(_ffi.lib().lb_moments_adjoint(ctx.handle, _ptr(f, ctx.dtype), _ptr(gbar, torch.float64),
                                          c_uint(mask), _ptr(lam, torch.float64)), "lb_moments_adjoint")
     return lam
+
+
+def _sched_dict(s: LbSchedule) -> dict:
+    return {"tile_width": s.tile_width, "blocks_per_sm": s.blocks_per_sm,
+            "persistent": s.persistent, "ms_per_step": s.ms_per_step}
+
+
+def lb_set_schedule(ctx: Context, tile_width: int = 128, blocks_per_sm: int = 0, persistent: int = 0):
+    s = LbSchedule(int(tile_width), int(blocks_per_sm), int(persistent), 0.0)
+    _check(_ffi.lib().lb_set_schedule(ctx.handle, byref(s)), "lb_set_schedule")
+
+
+def lb_get_schedule(ctx: Context) -> dict:
+    s = LbSchedule()
+    _check(_ffi.lib().lb_get_schedule(ctx.handle, byref(s)), "lb_get_schedule")
+    return _sched_dict(s)
+
+
+def lb_autotune(ctx: Context, f_a, f_b, trial_steps: int = 20) -> dict:
+    """Time the candidate schedules on f_a/f_b (advanced in place), keep and return the best."""
+    s = LbSchedule()
+    _check(_ffi.lib().lb_autotune(ctx.handle, _ptr(f_a, ctx.dtype), _ptr(f_b, ctx.dtype), int(trial_steps),
+                                  byref(s)), "lb_autotune")
+    return _sched_dict(s)
+
+
+def lb_step_graph(ctx: Context, f_a, f_b, nsteps: int):
+    _check(_ffi.lib().lb_step_graph(ctx.handle, _ptr(f_a, ctx.dtype), _ptr(f_b, ctx.dtype), int(nsteps)),
+           "lb_step_graph")
+    return f_b if nsteps % 2 == 1 else f_a
+
+
+def lb_test_barrier_timeout(ctx: Context, f_a, f_b):
+    _check(_ffi.lib().lb_test_barrier_timeout(ctx.handle, _ptr(f_a, ctx.dtype), _ptr(f_b, ctx.dtype)),
+           "lb_test_barrier_timeout")
 
 
 def lb_poll_status(ctx: Context):

@@ -1,0 +1,56 @@
+"""Persisted launch schedules for libsmrt's 1D-line kernels.
+
+lb_autotune (C++) times the candidate schedules of a context and applies the fastest. This
+module stores the result in a JSON file keyed by the GPU, velocity set, order, precision and
+the instance lengths, so that later runs of the same workload apply it without re-timing.
+The file is $SMRT_SCHEDULE_CACHE, else ~/.cache/smrt/schedules.json.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+from . import api
+
+
+def cache_path() -> str:
+    return os.environ.get("SMRT_SCHEDULE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "smrt", "schedules.json"))
+
+
+def schedule_key(ctx: api.Context, lengths) -> str:
+    import torch
+    gpu = torch.cuda.get_device_name(ctx.device)
+    h = hashlib.sha256(",".join(str(int(L)) for L in lengths).encode()).hexdigest()[:16]
+    return f"{gpu}|q{ctx.lattice.q}|N{ctx.N}|p{ctx.precision}|{len(lengths)}x{h}"
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def tuned_schedule(ctx: api.Context, f, lengths, trial_steps: int = 20, path: str | None = None,
+                   retune: bool = False) -> dict:
+    """Apply the cached schedule for this workload, or autotune on copies of the state f (f is
+    left untouched) and cache the winner. Returns the schedule applied."""
+    path = path or cache_path()
+    key = schedule_key(ctx, lengths)
+    db = _load(path)
+    if key in db and not retune:
+        s = db[key]
+        api.lb_set_schedule(ctx, s["tile_width"], s["blocks_per_sm"], s["persistent"])
+        return s
+    fa, fb = f.clone(), ctx.new_state()
+    best = api.lb_autotune(ctx, fa, fb, trial_steps)
+    db[key] = best
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(db, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs<Lat, T> A) {
     }
     for (int k = 0; k < KT; ++k) red[k][threadIdx.x] = tb[k];
     __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {  // blockDim.x: 32, 64 or 128
         if ((int)threadIdx.x < w)
             for (int k = 0; k < KT; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
         __syncthreads();

@@ -46,11 +46,27 @@ struct lb_ctx {
     void *d_ghosts;
     double *d_ghostsd;
     double *d_states;
-    unsigned *d_health;
+    unsigned *d_health;  // [0] health flags, [1..3] grid barrier and step counter
     double *d_partials;  // per-block relaxation-time gradients of lb_step_adjoint
+    long long max_tiles; // tile capacity (32-cell tiles) of d_tiles and d_partials
+    lb_schedule sched;
+    int num_sms;
+    // cached graph of the persistent launch (lb_step_graph)
+    cudaGraphExec_t graph;
+    cudaStream_t capture_stream;
+    const void *graph_fa, *graph_fb;
+    int graph_steps;
+    lb_schedule graph_sched;
 };
 
 namespace {
+
+std::vector<int2> make_tiles(const std::vector<int> &nx_inst, int width) {
+    std::vector<int2> tiles;
+    for (int j = 0; j < (int)nx_inst.size(); ++j)
+        for (int x0 = 0; x0 < nx_inst[j]; x0 += width) tiles.push_back(make_int2(j, x0));
+    return tiles;
+}
 
 template <class Lat>
 bool match_set(const lb_lattice_desc *d, std::vector<int> &perm) {
@@ -96,6 +112,8 @@ void free_tables(lb_ctx *c) {
     cudaFree(c->d_states);
     cudaFree(c->d_health);
     cudaFree(c->d_partials);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
 }
 
 }  // namespace
@@ -198,10 +216,14 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         in.cell_off = (long long)ncells;
         in.nx = c->nx_inst[j];
         in.kx = k0;
-        if (line)
-            for (int x0 = 0; x0 < in.nx; x0 += kTile) tiles.push_back(make_int2(j, x0));
         ncells += line ? (size_t)in.nx : (size_t)grid->nx * grid->ny * grid->nz;
     }
+    if (line) tiles = make_tiles(c->nx_inst, kTile);
+    c->max_tiles = line ? (long long)make_tiles(c->nx_inst, 32).size() : 0;
+    c->sched.tile_width = kTile;
+    c->sched.blocks_per_sm = 0;
+    c->sched.persistent = 0;
+    c->sched.ms_per_step = 0.0;
     c->ncells = ncells;
     c->stride = (ncells + 63) / 64 * 64;  // planes start on 256-byte boundaries (float)
     c->h_states.assign((size_t)grid->batch * 10, 0.0);
@@ -223,15 +245,22 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     v.fixedx = grid->bc_x;
     v.ntiles = (int)tiles.size();
     v.ncells = (long long)ncells;
+    v.tile_width = kTile;
 
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&c->d_inst, sizeof(InstanceInfo) * grid->batch);
-    if (e == cudaSuccess && !tiles.empty()) e = cudaMalloc(&c->d_tiles, sizeof(int2) * tiles.size());
+    if (e == cudaSuccess && line) e = cudaMalloc(&c->d_tiles, sizeof(int2) * c->max_tiles);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghosts, c->elem * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghostsd, sizeof(double) * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_states, sizeof(double) * 10 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_health, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_partials, sizeof(double) * kMaxTau * std::max(1LL, adj_blocks(v)));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_partials, sizeof(double) * kMaxTau * std::max(1LL, line ? c->max_tiles : adj_blocks(v)));
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e != cudaSuccess) {
         free_tables(c);
         delete c;
@@ -257,6 +286,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     v.ghosts = c->d_ghosts;
     v.ghostsd = c->d_ghostsd;
     v.health = c->d_health;
+    v.bar = c->d_health + 1;
     c->relax_set = false;
     *out = c;
     return LB_OK;
@@ -333,12 +363,40 @@ extern "C" lb_status lb_fill_equilibrium(lb_ctx *c, void *f, const double *rho, 
     return cuda_status(c->ks->fill(c->view, f, rho, u, theta));
 }
 
-extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
+namespace {
+
+lb_status check_pair(const lb_ctx *c, const void *fa, const void *fb, int nsteps) {
     if (!c || !fa || !fb || fa == fb || nsteps < 1) return LB_ERR_INVALID;
     if (!c->relax_set) return LB_ERR_INVALID;
     const size_t bytes = c->elem * lb_state_elems(c);
     const char *a0 = static_cast<const char *>(fa), *b0 = static_cast<const char *>(fb);
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;  // overlap
+    return LB_OK;
+}
+
+// grid of the persistent launch: blocks_per_sm (0 = as many as fit) on every SM, at most one
+// block per tile
+long long persistent_grid(const lb_ctx *c) {
+    const int occ = c->ks->occupancy(c->view);
+    if (occ < 1) return 0;
+    const int bps = c->sched.blocks_per_sm > 0 ? std::min(c->sched.blocks_per_sm, occ) : occ;
+    return std::max(1LL, std::min((long long)bps * c->num_sms, (long long)c->view.ntiles));
+}
+
+cudaError_t launch_persistent(lb_ctx *c, const CtxView &v, void *fa, void *fb, int nsteps) {
+    const long long grid = persistent_grid(c);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaMemsetAsync(c->d_health + 1, 0, sizeof(unsigned), v.stream);  // arrivals
+    if (e == cudaSuccess) e = c->ks->persist(v, fa, fb, nsteps, (int)grid);
+    return e;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
+    const lb_status st = check_pair(c, fa, fb, nsteps);
+    if (st != LB_OK) return st;
+    if (c->view.line && c->sched.persistent) return cuda_status(launch_persistent(c, c->view, fa, fb, nsteps));
     void *src = fa, *dst = fb;
     for (int s = 0; s < nsteps; ++s) {
         c->view.step++;
@@ -347,6 +405,147 @@ extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
         std::swap(src, dst);
     }
     return LB_OK;
+}
+
+extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
+    if (!c || !s) return LB_ERR_INVALID;
+    if (s->tile_width != 32 && s->tile_width != 64 && s->tile_width != 128) return LB_ERR_INVALID;
+    if (s->blocks_per_sm < 0 || (s->persistent != 0 && s->persistent != 1)) return LB_ERR_INVALID;
+    if (!c->view.line) {  // the box kernel has one fixed launch shape
+        if (s->persistent || s->tile_width != kTile) return LB_ERR_UNSUPPORTED;
+        c->sched = *s;
+        return LB_OK;
+    }
+    if (s->tile_width != c->view.tile_width) {
+        const std::vector<int2> tiles = make_tiles(c->nx_inst, s->tile_width);
+        if ((long long)tiles.size() > c->max_tiles) return LB_ERR_INVALID;
+        cudaError_t e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                                        cudaMemcpyHostToDevice, c->view.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
+        if (e != cudaSuccess) return LB_ERR_CUDA;
+        c->view.ntiles = (int)tiles.size();
+        c->view.tile_width = s->tile_width;
+    }
+    c->sched = *s;
+    if (c->sched.persistent && c->ks->occupancy(c->view) < 1) {
+        c->sched.persistent = 0;
+        return LB_ERR_UNSUPPORTED;
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_get_schedule(const lb_ctx *c, lb_schedule *s) {
+    if (!c || !s) return LB_ERR_INVALID;
+    *s = c->sched;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_autotune(lb_ctx *c, void *fa, void *fb, int trial_steps, lb_schedule *best) {
+    lb_status st = check_pair(c, fa, fb, 2);
+    if (st != LB_OK || trial_steps < 1 || !best) return st != LB_OK ? st : LB_ERR_INVALID;
+    std::vector<lb_schedule> cand;
+    const int widths[3] = {32, 64, 128};
+    const int nwidths = c->view.line ? 3 : 1;
+    for (int wi = 0; wi < nwidths; ++wi) {
+        const int width = c->view.line ? widths[wi] : kTile;
+        cand.push_back(lb_schedule{width, 0, 0, 0.0});  // one launch per step
+        if (!c->view.line) continue;
+        const lb_schedule probe{width, 0, 1, 0.0};
+        if (lb_set_schedule(c, &probe) != LB_OK) continue;
+        const int occ = c->ks->occupancy(c->view);
+        const int opts[4] = {1, 2, 4, occ};
+        for (int bps : opts) {
+            if (bps < 1 || bps > occ) continue;
+            bool dup = false;
+            for (const lb_schedule &q : cand)
+                dup = dup || (q.tile_width == width && q.persistent && q.blocks_per_sm == bps);
+            if (!dup) cand.push_back(lb_schedule{width, bps, 1, 0.0});  // persistent launch
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LB_ERR_CUDA;
+    }
+    int pick = -1;
+    void *src = fa, *dst = fb;
+    for (size_t k = 0; k < cand.size(); ++k) {
+        if (lb_set_schedule(c, &cand[k]) != LB_OK) continue;
+        // warm up, then time trial_steps; an even step count keeps the state in src
+        const int n = trial_steps + (trial_steps & 1);
+        if (lb_step(c, src, dst, 2) != LB_OK) break;
+        cudaEventRecord(e0, c->view.stream);
+        if (lb_step(c, src, dst, n) != LB_OK) break;
+        cudaEventRecord(e1, c->view.stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cand[k].ms_per_step = ms / n;
+        if (pick < 0 || cand[k].ms_per_step < cand[pick].ms_per_step) pick = (int)k;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (pick < 0) return LB_ERR_CUDA;
+    st = lb_set_schedule(c, &cand[pick]);
+    *best = cand[pick];
+    return st;
+}
+
+extern "C" lb_status lb_test_barrier_timeout(lb_ctx *c, void *fa, void *fb) {
+    const lb_status st = check_pair(c, fa, fb, 2);
+    if (st != LB_OK) return st;
+    if (!c->view.line) return LB_ERR_UNSUPPORTED;
+    const long long grid = persistent_grid(c);
+    if (grid < 1) return LB_ERR_UNSUPPORTED;
+    // preset the arrival count past the grid size: the barrier after the first step can never
+    // complete, so every block waits out its bounded spin, flags the timeout and returns
+    const unsigned never = 0x7fffffffu;
+    cudaError_t e = cudaMemcpyAsync(c->d_health + 1, &never, sizeof(unsigned), cudaMemcpyHostToDevice, c->view.stream);
+    if (e == cudaSuccess) e = c->ks->persist(c->view, fa, fb, 2, (int)grid);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
+    return cuda_status(e);
+}
+
+extern "C" lb_status lb_step_graph(lb_ctx *c, void *fa, void *fb, int nsteps) {
+    const lb_status st = check_pair(c, fa, fb, nsteps);
+    if (st != LB_OK) return st;
+    if (!c->view.line) return LB_ERR_UNSUPPORTED;
+    const bool same = c->graph && c->graph_fa == fa && c->graph_fb == fb && c->graph_steps == nsteps &&
+                      c->graph_sched.tile_width == c->sched.tile_width &&
+                      c->graph_sched.blocks_per_sm == c->sched.blocks_per_sm;
+    if (!same) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaError_t e = cudaSuccess;
+        if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return LB_ERR_CUDA;
+        CtxView v = c->view;
+        v.stream = c->capture_stream;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return LB_ERR_CUDA;
+        const cudaError_t el = launch_persistent(c, v, fa, fb, nsteps);
+        e = cudaStreamEndCapture(c->capture_stream, &g);
+        if (el != cudaSuccess || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return LB_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return LB_ERR_CUDA;
+        }
+        c->graph_fa = fa;
+        c->graph_fb = fb;
+        c->graph_steps = nsteps;
+        c->graph_sched = c->sched;
+    }
+    return cuda_status(cudaGraphLaunch(c->graph, c->view.stream));
 }
 
 extern "C" lb_status lb_moments(lb_ctx *c, const void *f, double *out, unsigned mask) {

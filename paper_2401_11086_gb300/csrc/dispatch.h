@@ -29,7 +29,9 @@ struct CtxView {
     const double *ghostsd;  // end-state deviations in double
     unsigned *health;
     long long ncells;
-    unsigned step;  // launch counter of lb_step (seeds the stochastic rounding)
+    unsigned step;   // launch counter of lb_step (seeds the stochastic rounding)
+    int tile_width;  // cells (threads) per block of the line kernels: 32, 64 or 128
+    unsigned *bar;   // persistent launch: arrival count, generation, step counter
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
@@ -39,11 +41,16 @@ using FillFn = cudaError_t (*)(const CtxView &, void *f, const double *rho, cons
 using GhostFn = cudaError_t (*)(const CtxView &, const double *states, int ninst, void *ghosts,
                                 double *ghostsd);
 
+using PersistFn = cudaError_t (*)(const CtxView &, void *fa, void *fb, int nsteps, int grid);
+using OccupancyFn = int (*)(const CtxView &);
+
 struct KernelSet {
     StepFn step;
     MomentsFn moments;
     FillFn fill;
     GhostFn ghost;
+    PersistFn persist;      // line geometry: all steps in one cooperative launch
+    OccupancyFn occupancy;  // resident blocks per SM of the persistent kernel
 };
 
 // precision: 0 double, 1 float, 2 float with double conserved sums and equilibrium rebuild
@@ -82,9 +89,9 @@ cudaError_t launch_step(const CtxView &v, const void *fin, void *fout) {
     const StepArgs<Lat, T> a = make_args<Lat, T>(v, fin, fout);
     if (v.line) {
         if (v.fixedx)
-            step_line_kernel<Lat, N, T, Acc, Split, true><<<v.ntiles, kTile, 0, v.stream>>>(a);
+            step_line_kernel<Lat, N, T, Acc, Split, true><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
         else
-            step_line_kernel<Lat, N, T, Acc, Split, false><<<v.ntiles, kTile, 0, v.stream>>>(a);
+            step_line_kernel<Lat, N, T, Acc, Split, false><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
     } else {
         const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
         step_box_kernel<Lat, N, T, Acc, Split><<<grid, kTile, 0, v.stream>>>(a);
@@ -102,7 +109,7 @@ cudaError_t launch_moments(const CtxView &v, const void *f, double *out, unsigne
     m.line = v.line;
     m.fixedx = v.fixedx;
     if (v.line) {
-        moments_kernel<Lat, N, T, Acc><<<v.ntiles, kTile, 0, v.stream>>>(m);
+        moments_kernel<Lat, N, T, Acc><<<v.ntiles, v.tile_width, 0, v.stream>>>(m);
     } else {
         const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
         moments_kernel<Lat, N, T, Acc><<<grid, kTile, 0, v.stream>>>(m);
@@ -115,7 +122,7 @@ cudaError_t launch_fill(const CtxView &v, void *f, const double *rho, const doub
                         const double *theta) {
     const StepArgs<Lat, T> a = make_args<Lat, T>(v, nullptr, f);
     if (v.line) {
-        fill_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(a, rho, u, theta, v.ncells, 1);
+        fill_kernel<Lat, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(a, rho, u, theta, v.ncells, 1);
     } else {
         const long long nb = (v.ncells + kTile - 1) / kTile;
         fill_kernel<Lat, N, T><<<(unsigned)nb, kTile, 0, v.stream>>>(a, rho, u, theta, v.ncells, 0);
@@ -132,13 +139,48 @@ cudaError_t launch_ghost(const CtxView &v, const double *states, int ninst, void
     return cudaGetLastError();
 }
 
+// One cooperative launch (all blocks resident; the launch fails rather than waits when they
+// do not fit) running nsteps steps of every tile; the state ends in fb for odd nsteps.
+template <class Lat, int N, class T, class Acc, bool Split>
+cudaError_t launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, int grid) {
+    const StepArgs<Lat, T> a = make_args<Lat, T>(v, fa, fb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(v.tile_width);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = v.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int ntiles = v.ntiles;
+    unsigned *bar = v.bar;
+    if (v.fixedx)
+        return cudaLaunchKernelEx(&cfg, step_line_persistent<Lat, N, T, Acc, Split, true>, a, nsteps, ntiles, bar);
+    return cudaLaunchKernelEx(&cfg, step_line_persistent<Lat, N, T, Acc, Split, false>, a, nsteps, ntiles, bar);
+}
+
+template <class Lat, int N, class T, class Acc, bool Split>
+int persistent_occupancy(const CtxView &v) {
+    int n = 0;
+    const cudaError_t e =
+        v.fixedx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_line_persistent<Lat, N, T, Acc, Split, true>,
+                                                                 v.tile_width, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_line_persistent<Lat, N, T, Acc, Split, false>,
+                                                                 v.tile_width, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
 template <class Lat, int N, int P>
 const KernelSet *kernel_set() {
     using T = typename std::conditional<P == 0, double, float>::type;
     using Acc = typename std::conditional<P == 1, float, double>::type;
     constexpr bool Split = (P == 2);
     static const KernelSet ks = {&launch_step<Lat, N, T, Acc, Split>, &launch_moments<Lat, N, T, Acc>,
-                                 &launch_fill<Lat, N, T>, &launch_ghost<Lat, N, T>};
+                                 &launch_fill<Lat, N, T>, &launch_ghost<Lat, N, T>,
+                                 &launch_persistent<Lat, N, T, Acc, Split>,
+                                 &persistent_occupancy<Lat, N, T, Acc, Split>};
     return &ks;
 }
 
@@ -187,7 +229,7 @@ cudaError_t launch_adj_step(const CtxView &v, const void *f, const double *lam_n
     A.lam_out = lam_t;
     A.partials = partials;
     if (v.line) {
-        adjoint_step_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(A);
+        adjoint_step_kernel<Lat, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(A);
     } else {
         const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
         adjoint_step_kernel<Lat, N, T><<<grid, kTile, 0, v.stream>>>(A);
@@ -205,7 +247,7 @@ cudaError_t launch_adj_moments(const CtxView &v, const void *f, const double *gb
     A.lam_out = lam;
     A.mask = mask;
     if (v.line) {
-        adjoint_moments_kernel<Lat, N, T><<<v.ntiles, kTile, 0, v.stream>>>(A);
+        adjoint_moments_kernel<Lat, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(A);
     } else {
         const dim3 grid((v.nx + kTile - 1) / kTile, v.ny, v.nz);
         adjoint_moments_kernel<Lat, N, T><<<grid, kTile, 0, v.stream>>>(A);

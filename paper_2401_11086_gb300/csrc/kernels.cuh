@@ -447,10 +447,21 @@ __global__ void __launch_bounds__(128) step_box_kernel(StepArgs<Lat, T> a) {
 
 // Batched 1D lines (ny = nz = 1): block b handles cells x0 .. x0+blockDim-1 of instance j,
 // (j, x0) = tiles[b]. FixedX: pulls from beyond either end read the end-state populations.
-template <class Lat, int N, class T, class Acc, bool Split, bool FixedX>
-__global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
+// Coherent: read the previous state through L2 only (__ldcg). Inside a persistent launch a
+// buffer is rewritten between two reads by the same SM, and L1 is not kept coherent.
+template <bool Coherent, class T>
+SMRT_D T load_pop(const T *p) {
+    if constexpr (Coherent)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+template <class Lat, int N, class T, class Acc, bool Split, bool FixedX, bool Coherent = false>
+SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *__restrict__ fout,
+                      int tile_index, unsigned step) {
     using C = Collide<Lat, N, T, Acc, Split>;
-    const int2 tile = a.tiles[blockIdx.x];
+    const int2 tile = a.tiles[tile_index];
     const InstanceInfo &in = a.inst[tile.x];
     const int x = tile.y + threadIdx.x;
     const int L = in.nx;
@@ -474,10 +485,10 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
                 f[0] = gr[0];
                 if constexpr (Res) res[0] = Acc(grd[0]) - Acc(gr[0]);
             } else {
-                f[0] = a.fin[a.plane[0] + base + xs];
+                f[0] = load_pop<Coherent>(fin + a.plane[0] + base + xs);
             }
         } else {
-            f[0] = a.fin[a.plane[0] + base + wrap(xs, L)];
+            f[0] = load_pop<Coherent>(fin + a.plane[0] + base + wrap(xs, L));
         }
     }
     static_for<Lat::NP>([&](auto P) {
@@ -494,20 +505,82 @@ __global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
                     f[i] = gr[i];
                     if constexpr (Res) res[i] = Acc(grd[i]) - Acc(gr[i]);
                 } else {
-                    f[i] = a.fin[a.plane[i] + base + xs];
+                    f[i] = load_pop<Coherent>(fin + a.plane[i] + base + xs);
                 }
             } else {
-                f[i] = a.fin[a.plane[i] + base + wrap(xs, L)];
+                f[i] = load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L));
             }
         });
     });
     const bool ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
-                               mix32(unsigned(base + x) ^ mix32(a.step)), Res ? res : nullptr);
+                               mix32(unsigned(base + x) ^ mix32(step)), Res ? res : nullptr);
     if (!ok) atomicOr(a.health, 1u);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        a.fout[a.plane[i] + base + x] = f[i];
+        fout[a.plane[i] + base + x] = f[i];
     });
+}
+
+template <class Lat, int N, class T, class Acc, bool Split, bool FixedX>
+__global__ void __launch_bounds__(128) step_line_kernel(StepArgs<Lat, T> a) {
+    line_tile<Lat, N, T, Acc, Split, FixedX>(a, a.fin, a.fout, blockIdx.x, a.step);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident). bar[0] counts arrivals,
+// bar[1] is the generation. The spin gives up after about a second: it then records
+// LB_HEALTH_TIMEOUT and returns false, and the caller leaves the kernel.
+SMRT_D bool grid_barrier(unsigned *bar, unsigned &gen, unsigned *health) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        const unsigned target = gen + 1u;
+        if (atomicAdd(&bar[0], 1u) + 1u == gridDim.x) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], target);
+        } else {
+            unsigned spins = 0;
+            while (atomicAdd(&bar[1], 0u) != target) {
+                if (++spins > (1u << 22)) {  // ~1 s at 256 ns per spin
+                    atomicOr(health, 2u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        gen = target;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Persistent batched step: one cooperative launch runs nsteps steps of every tile of a batch
+// of 1D lines, tiles distributed over the blocks (grid-stride), a grid barrier between steps.
+// bar[2] holds the running step counter (seeds the stochastic rounding across launches).
+template <class Lat, int N, class T, class Acc, bool Split, bool FixedX>
+__global__ void __launch_bounds__(128) step_line_persistent(StepArgs<Lat, T> a, int nsteps, int ntiles,
+                                                            unsigned *bar) {
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = atomicAdd(&bar[1], 0u);
+    const unsigned step0 = __ldcg(&bar[2]);
+    const T *src = a.fin;
+    T *dst = a.fout;
+    for (int s = 0; s < nsteps; ++s) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+            line_tile<Lat, N, T, Acc, Split, FixedX, true>(a, src, dst, t, step0 + unsigned(s));
+        if (s + 1 < nsteps) {
+            if (!grid_barrier(bar, gen, a.health)) return;
+            // next step reads what this one wrote; swap buffers (f_a -> f_b -> f_a ...)
+            const T *nsrc = dst;
+            dst = (dst == a.fout) ? const_cast<T *>(a.fin) : a.fout;
+            src = nsrc;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bar[2] = step0 + unsigned(nsteps);
 }
 
 // ------------------------------------------------------------------------------ moments

@@ -222,3 +222,19 @@ extern "C" lb_status lb_rankine_hugoniot(double Ma, double gamma, double rho1, d
     *right = lb_state{rho1 * r, {u1 / r, 0.0, 0.0}, theta1 * t};
     return LB_OK;
 }
+
+extern "C" lb_status lb_shock_frame(double Ma, double gamma, double c, double theta2_max, double *theta1,
+                                    int *kx) {
+    if (!theta1 || !kx || !(Ma >= 1.0) || !(gamma > 1.0) || !(c > 0.0) || !(theta2_max > 0.0))
+        return LB_ERR_INVALID;
+    lb_state l, r;
+    lb_rankine_hugoniot(Ma, gamma, 1.0, 1.0, &l, &r);
+    const double ratio = r.theta;  // theta2 / theta1
+    // the hottest state must stay below the convergence bound theta < 2 (Sec. 4.1)
+    const double t1 = (ratio < 2.0 && Ma <= 1.9) ? 1.0 : theta2_max / ratio;
+    const double c1 = std::sqrt(gamma * t1);
+    const double mean = (gamma * Ma * Ma + 1.0) / ((gamma + 1.0) * Ma) * c1;  // (u1 + u2) / 2
+    *theta1 = t1;
+    *kx = (int)std::lround(mean / c);
+    return LB_OK;
+}

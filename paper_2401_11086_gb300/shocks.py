@@ -1,0 +1,76 @@
+"""Set-up of 1D normal-shock problems on libsmrt contexts (Sec. 4.2 of Yan & Shan).
+
+Problem set-up only (end states, frame shift, relaxation times, initial fields); every step of
+the method runs in libsmrt. A shock of upstream Mach number Ma in a monatomic gas
+(gamma = 5/3) has Rankine-Hugoniot end states (lb_rankine_hugoniot), a reference temperature
+and integer frame shift chosen by lb_shock_frame, and relaxation times from Table 4 scaled by
+the upstream mean free path: ell cells = tau_c,20 sqrt(theta1) / c.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import api
+
+GAMMA = 5.0 / 3.0
+
+# Table 4: tau*_{n,m} = tau_{n,m} / tau_{2,0}, Maxwell molecules (SMRT) and the Shakhov model,
+# in lb_set_relaxation's order (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2). tau_{2,1} (bulk) is
+# absent for a monatomic gas; its mode vanishes identically, 1 is used.
+TAU_RATIOS_SMRT = (1.0, 1.0, 2.0 / 3.0, 3.0 / 2.0, 432.0 / 763.0, 6.0 / 7.0, 3.0 / 2.0)
+TAU_RATIOS_SHAKHOV = (1.0, 1.0, 1.0, 3.0 / 2.0, 1.0, 1.0, 1.0)
+
+
+def ntau(N: int) -> int:
+    return sum(n // 2 + 1 for n in range(2, N + 1))
+
+
+def shock_params(Ma: float, c: float, N: int, ell_cells: float = 2.0, ratios=TAU_RATIOS_SMRT,
+                 theta2_max: float = 1.2):
+    """End states, frame shift and continuous relaxation times of one shock."""
+    theta1, kx = api.lb_shock_frame(Ma, c, GAMMA, theta2_max)
+    left, right = api.lb_rankine_hugoniot(Ma, GAMMA, 1.0, theta1)
+    tau20 = ell_cells * c / np.sqrt(theta1)
+    taus = [r * tau20 for r in ratios[: ntau(N)]]
+    return {"Ma": Ma, "theta1": theta1, "kx": kx, "left": left, "right": right, "taus": taus}
+
+
+def tanh_fields(params, L: int, width: float):
+    """rho, u_x, theta of the tanh blend between the end states (x0 = L/2)."""
+    x = np.arange(L, dtype=np.float64)
+    s = 0.5 * (1.0 + np.tanh((x - L / 2.0) / width))
+    lf, rt = params["left"], params["right"]
+    rho = lf["rho"] + (rt["rho"] - lf["rho"]) * s
+    u = lf["u"][0] + (rt["u"][0] - lf["u"][0]) * s
+    th = lf["theta"] + (rt["theta"] - lf["theta"]) * s
+    return rho, u, th
+
+
+def setup_batch(lattice: api.LatticeDesc, N: int, machs, lengths, precision: str = "f32c64",
+                ell_cells: float = 2.0, width: float = 10.0, stream=None):
+    """A batched context with one shock per (Ma, L) and its initial state: the equilibrium of
+    the tanh blend of width `width` cells (10 by default: a wider blend puts intermediate
+    (u, theta) states into the cells that, above Ma ~ 3.5, leave the stable range of a degree-9
+    velocity set). Returns (ctx, state, per-instance params)."""
+    import torch
+    lat = api.LatticeDesc(lattice.e, lattice.w, lattice.c, lattice.degree, (0, 0, 0))
+    ctx = api.lb_init_lattice(lat, 0, N=N, precision=precision, bc_x=1,
+                              nx_per_instance=[int(L) for L in lengths], stream=stream)
+    params = []
+    rho, ux, th = [], [], []
+    for j, (Ma, L) in enumerate(zip(machs, lengths)):
+        p = shock_params(float(Ma), lattice.c, N, ell_cells)
+        api.lb_set_frame_shift(ctx, j, p["kx"])
+        api.lb_set_relaxation(ctx, p["taus"], True, 1.0, p["left"], p["right"], instance=j)
+        r, u, t = tanh_fields(p, int(L), width)
+        rho.append(r)
+        ux.append(u)
+        th.append(t)
+        params.append(p)
+    rho, ux, th = np.concatenate(rho), np.concatenate(ux), np.concatenate(th)
+    u = np.stack([ux, np.zeros_like(ux), np.zeros_like(ux)])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(ctx.device)  # noqa: E731
+    f = ctx.new_state()
+    api.lb_fill_equilibrium(ctx, f, dev(rho), dev(u), dev(th))
+    ctx.relax_args = None  # per-instance relaxation: lb_set_relaxation was called per instance
+    return ctx, f, params

@@ -101,3 +101,13 @@ def test_unknown_lattice_is_unsupported(lib):
     o = OL.d3q729()
     assert _init(lib, o.e[:103], o.w[:103], o.c, 11) in (1, 5)
     assert lib.lb_lattice_named(b"D3Q729", None, None, None, None, None, 0) == 1
+
+
+@pytest.mark.parametrize("Ma", [1.2, 1.5, 1.9, 3.0, 5.0, 7.0])
+def test_library_shock_frame_agrees_with_oracle(lib, Ma):
+    import paper_2401_11086_gb300 as P
+    for name in ("D3Q39", "D3Q103"):
+        c = P.lb_lattice_named(name).c
+        t1, k = P.lb_shock_frame(Ma, c)
+        assert abs(t1 - OK.theta_scale(Ma)) < 1e-14
+        assert k == OK.shift(Ma, t1, c)
