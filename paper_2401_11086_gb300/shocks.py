@@ -14,6 +14,14 @@ from . import api
 
 GAMMA = 5.0 / 3.0
 
+# Largest upstream Mach number whose uniform states stay linearly stable on the degree-9
+# velocity set (D3Q103, N = 4, theta2 = 1.2, ell = 2 cells): seeded 1e-6 noise on a periodic
+# line at the upstream state stays flat at Ma = 3.0 and grows tenfold every 300 steps at 3.25;
+# at Ma = 5 it overflows within 600 steps. Long domains (thousands of cells) let that growth
+# run to completion, so batched long shocks on this set use Ma <= 3. The paper's own runs at
+# Ma 5 and 7 use degree-11 and degree-19 sets.
+MA_STABLE_DEGREE9 = 3.0
+
 # Table 4: tau*_{n,m} = tau_{n,m} / tau_{2,0}, Maxwell molecules (SMRT) and the Shakhov model,
 # in lb_set_relaxation's order (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2). tau_{2,1} (bulk) is
 # absent for a monatomic gas; its mode vanishes identically, 1 is used.

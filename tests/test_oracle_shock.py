@@ -82,3 +82,28 @@ def test_converged_shock_is_steady_and_satisfies_rankine_hugoniot(converged_shoc
     # the profile is monotone and the heat flux inside the shock is negative (flows upstream)
     assert np.all(np.diff(m["rho"]) > -1e-9)
     assert m["q"][0][pos] < 0.0
+
+
+def _upstream_noise_growth(Ma, steps=600):
+    """Max relative density deviation after `steps` steps of the uniform upstream state of a
+    Ma shock (D3Q103, N = 4, theta2 = 1.2, ell = 2 cells) seeded with 1e-6 noise, periodic."""
+    lat = L.d3q103()
+    nx = 64
+    case = K.shock_case(lat, 4, Ma, nx)
+    st = case.states
+    rng = np.random.default_rng(0)
+    rho = st["rho1"] * (1 + 1e-6 * rng.standard_normal(nx))
+    u = np.stack([np.full(nx, st["u1"] - lat.c * case.k), np.zeros(nx), np.zeros(nx)])
+    h = S.equilibrium(rho, u, np.full(nx, st["theta1"]), lat, 4).reshape(lat.q, 1, 1, nx)
+    geom = S.Geometry(shape=(1, 1, nx), shift=(case.k, 0, 0))
+    for _ in range(steps):
+        h = S.step(h, case.model, geom)
+    m = S.macroscopic(h, case.model, geom)
+    return float(np.max(np.abs(m["rho"] / st["rho1"] - 1)))
+
+
+def test_degree9_upstream_stability_boundary():
+    """The batched shocks use Ma <= 3 on the degree-9 set: at Ma 2.5 seeded noise stays at its
+    initial level, at Ma 3.25 it has grown more than tenfold after 600 steps."""
+    assert _upstream_noise_growth(2.5) < 2e-6
+    assert _upstream_noise_growth(3.25) > 1e-5
