@@ -189,6 +189,27 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def batched_instances(rank: int):
+    """The 64 shocks of one rank: Mach numbers and lengths drawn with seed 11086 + rank (each
+    rank owns its own independent instances), Ma within the degree-9 set's stable range."""
+    import synthetic
+    from paper_2401_11086_gb300.shocks import MA_STABLE_DEGREE9
+    return synthetic.batched_shocks(seed=synthetic.SEED + rank, ma_range=(1.2, MA_STABLE_DEGREE9))
+
+
+def job_rate(units: float, ms: float, dist=None, device="cuda"):
+    """Whole-job throughput: all ranks' units / the slowest rank's time. Returns (units per
+    second, max ms). Without a process group, the local numbers."""
+    if dist is None:
+        return units / (ms * 1e-3), ms
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / (float(t.item()) * 1e-3), float(t.item())
+
+
 def oracle_shock_rate(L: int, steps: int) -> dict:
     """FP64 oracle on one Ma = 3 shock of L cells (D3Q103, N = 4), single-threaded BLAS."""
     code = f"""
@@ -232,10 +253,9 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # weak scaling: every rank runs its own 64 shocks (the seeded set, shifted by rank so that
-    # the ranks' instances differ); instances are independent, so there is no exchange
-    machs, lengths = synthetic.batched_shocks(seed=synthetic.SEED + rank,
-                                              ma_range=(1.2, shocks.MA_STABLE_DEGREE9))
+    # weak scaling: every rank runs its own 64 shocks; instances are independent, so there is
+    # no exchange
+    machs, lengths = batched_instances(rank)
     d = P.lb_lattice_named("D3Q103")
     stream = torch.cuda.current_stream()
     ctx, f0, _ = shocks.setup_batch(d, 4, machs, lengths, precision="f32c64", stream=stream)
@@ -260,13 +280,10 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
     st, flags = P.lb_poll_status(ctx)
     if st != 0:
         raise SystemExit(f"health word reports status {st} (flags {flags})")
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     cells = int(lengths.sum())
     q = 103
-    value = world * cells * q * K / (ms * 1e-3) / 1e9
+    rate, ms = job_rate(cells * q * K, ms, dist)
+    value = rate / 1e9
     peak, peak_kind = measured_peak()
     achieved = 2.0 * q * 4 * cells * K / (ms * 1e-3) / 1e9
     if rank != 0:
@@ -372,13 +389,9 @@ def main():
     if st != 0:
         raise SystemExit(f"health word reports status {st} (flags {flags})")
 
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
     cells = n ** 3
-    value = world * cells * Q * K / (total_ms * 1e-3) / 1e9
+    rate, total_ms = job_rate(cells * Q * K, total_ms, dist)
+    value = rate / 1e9
 
     # end to end through the public API with host buffers: every step copies the state in from
     # pinned host memory, steps once, and copies the new state back
