@@ -96,8 +96,12 @@ typedef struct {
 /* lb_init_lattice -- create a context for one velocity set, grid, truncation order and
  * precision. The velocity set must integrate every monomial of degree <= 2N exactly (Sec. 3,
  * the exactness remark after Eq. fi); the library checks this by brute force and also
- * matches e against the velocity sets it has kernels for (LB_ERR_UNSUPPORTED otherwise).
- * hermite_order N: truncation order of Eqs. an/fi (2 <= N <= 4 in this build).
+ * matches e against the velocity sets it has kernels for (LB_ERR_UNSUPPORTED otherwise):
+ *   D3Q39 (N = 3), D3Q103 (N = 3, 4): every geometry and precision;
+ *   D3Q729, the tensor product of D1Q9-P1 (Sec. 4.2, Table 3: d = 9, degree 11), N = 4, 5:
+ *     batched 1D lines (ny = nz = 1), frame shift along x only, LB_F64 or LB_F32; weights
+ *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint.
+ * hermite_order N: truncation order of Eqs. an/fi.
  * cuda_stream: cudaStream_t used for every later call on this context.
  * On success *out is a new context (relaxation times unset: lb_set_relaxation must follow).
  * Errors: LB_ERR_INVALID (null/size/quadrature), LB_ERR_UNSUPPORTED, LB_ERR_NOMEM, LB_ERR_CUDA. */
@@ -107,7 +111,8 @@ lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lattice, const lb
 /* lb_set_relaxation -- relaxation times of the SMRT operator (Eq. SMRT) and end states.
  * tau: continuous relaxation times tau_c,nm in time steps at density rho_ref, one per
  *      irreducible part (n, m), n = 2..N, m = 0..floor(n/2), in the order
- *      (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2) (host memory; 2 entries for N=2, 4 for N=3, 7 for N=4). Table 4 gives tau_nm / tau_20 for Maxwell molecules.
+ *      (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2) (5,0) (5,1) (5,2) (host memory; 2 entries for
+ *      N=2, 4 for N=3, 7 for N=4, 10 for N=5). Table 4 gives tau_nm / tau_20 for Maxwell molecules.
  *      The discrete time of part (n,m) at a cell is tau_c,nm * s + 1/2, with s = rho_ref/rho
  *      when maxwell_molecule_law is 1 (viscosity proportional to temperature, Sec. 4.2) and
  *      s = 1 when it is 0. Every tau must be > 0.
@@ -247,8 +252,11 @@ size_t lb_state_elems(const lb_ctx *ctx);  /* elements of one state = q * plane_
 int lb_num_moment_rows(const lb_ctx *ctx, unsigned which_mask);
 
 /* lb_lattice_named -- the library's own velocity sets, solved from the even-moment
- * conditions of a degree-Q Gauss-Hermite rule (Sec. 3, Eq. an): "D3Q39" (degree 7) and
- * "D3Q103" (degree 9). Writes up to capacity velocities: e_out (capacity*3 int8), w_out
+ * conditions of a degree-Q Gauss-Hermite rule (Sec. 3, Eq. an): "D3Q39" (degree 7),
+ * "D3Q103" (degree 9) and "D3Q729" (degree 11, the 3D tensor product of the 1D rule D1Q9-P1
+ * on c {0, +-1, +-2, +-3, +-5} of Sec. 4.2 / Table 3, in the order i = a + 9 b + 81 c over the
+ * 1D indices a, b, c = rest, +1, -1, +2, -2, +3, -3, +5, -5).
+ * Writes up to capacity velocities: e_out (capacity*3 int8), w_out
  * (capacity doubles), *c_out, *q_out, *degree_out (host memory).
  * Errors: LB_ERR_INVALID (unknown name, null, capacity too small). */
 lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w_out, double *c_out,

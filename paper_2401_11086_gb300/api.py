@@ -46,7 +46,7 @@ class LatticeDesc:
 
 
 def lb_lattice_named(name: str) -> LatticeDesc:
-    cap = 256
+    cap = 4913
     e = (c_int8 * (3 * cap))()
     w = (c_double * cap)()
     c, q, deg = c_double(), c_int(), c_int()

@@ -21,12 +21,14 @@ const KernelSet *kernels_d3q39_p2(int N);
 const KernelSet *kernels_d3q103_p0(int N);
 const KernelSet *kernels_d3q103_p1(int N);
 const KernelSet *kernels_d3q103_p2(int N);
+const KernelSet *kernels_d3q729_p0(int N);
+const KernelSet *kernels_d3q729_p1(int N);
 }  // namespace smrt
 
 using namespace smrt;
 
 struct lb_ctx {
-    int kind;  // 0 D3Q39, 1 D3Q103
+    int kind;  // 0 D3Q39, 1 D3Q103, 2 D3Q729 (tensor product of D1Q9-P1)
     int q, np, N, degree;
     lb_precision prec;
     size_t elem;  // bytes per population value
@@ -43,6 +45,7 @@ struct lb_ctx {
     // device tables owned by the context
     InstanceInfo *d_inst;
     int2 *d_tiles;
+    int *d_plane;        // tensor-product sets: caller plane of each library population
     void *d_ghosts;
     double *d_ghostsd;
     double *d_states;
@@ -94,6 +97,37 @@ bool match_set(const lb_lattice_desc *d, std::vector<int> &perm) {
     return true;
 }
 
+// A tensor-product set (Sec. 4.2): every velocity (e_a, e_b, e_c) of the 1D rule's abscissae
+// present once, with weight w_a w_b w_c. The 1D weights are read off the axis velocities:
+// w(0,0,0) = w_0^3 and w(e_a,0,0) = w_a w_0^2.
+template <class L1>
+bool match_tensor(const lb_lattice_desc *d, std::vector<int> &perm, double (&w1)[kMaxQ1]) {
+    constexpr int Q1 = L1::Q1;
+    if (d->q != Q1 * Q1 * Q1) return false;
+    perm.assign(d->q, -1);
+    std::vector<char> used(d->q, 0);
+    for (int i = 0; i < d->q; ++i) {
+        const int a = i % Q1, b = (i / Q1) % Q1, cc = i / (Q1 * Q1);
+        int hit = -1;
+        for (int k = 0; k < d->q && hit < 0; ++k)
+            if (!used[k] && d->e[3 * k] == e1<L1>(a) && d->e[3 * k + 1] == e1<L1>(b) && d->e[3 * k + 2] == e1<L1>(cc))
+                hit = k;
+        if (hit < 0) return false;
+        used[hit] = 1;
+        perm[i] = hit;
+    }
+    const double w0 = std::cbrt(d->w[perm[0]]);
+    for (int a = 0; a < Q1; ++a) w1[a] = d->w[perm[a]] / (w0 * w0);
+    for (int a = Q1; a < kMaxQ1; ++a) w1[a] = 0.0;
+    for (int p = 0; p < L1::NP1; ++p)  // the rebuild folds +e and -e: they share a weight
+        if (std::fabs(w1[2 * p + 1] - w1[2 * p + 2]) > 1e-14 * w1[2 * p + 1]) return false;
+    for (int i = 0; i < d->q; ++i) {
+        const double want = w1[i % Q1] * w1[(i / Q1) % Q1] * w1[i / (Q1 * Q1)];
+        if (std::fabs(d->w[perm[i]] - want) > 1e-12 * want) return false;
+    }
+    return true;
+}
+
 template <class Lat>
 int max_reach(int axis) {
     int m = 0;
@@ -107,6 +141,7 @@ void free_tables(lb_ctx *c) {
     if (!c) return;
     cudaFree(c->d_inst);
     cudaFree(c->d_tiles);
+    cudaFree(c->d_plane);
     cudaFree(c->d_ghosts);
     cudaFree(c->d_ghostsd);
     cudaFree(c->d_states);
@@ -123,7 +158,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     if (!out || !lat || !grid || !lat->e || !lat->w) return LB_ERR_INVALID;
     *out = nullptr;
     if (prec != LB_F64 && prec != LB_F32 && prec != LB_F32_CONS64) return LB_ERR_INVALID;
-    if (!(lat->c > 0.0) || lat->q <= 0 || lat->q > kMaxQ) return LB_ERR_INVALID;
+    if (!(lat->c > 0.0) || lat->q <= 0 || lat->q > kMaxQTP) return LB_ERR_INVALID;
     if (N < 2 || lat->degree < 2 * N) return LB_ERR_INVALID;
     if (grid->batch < 1 || grid->nx < 0 || grid->ny < 1 || grid->nz < 1) return LB_ERR_INVALID;
     if (grid->bc_x != 0 && grid->bc_x != 1) return LB_ERR_INVALID;
@@ -140,7 +175,17 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     c->prec = prec;
     c->elem = prec == LB_F64 ? sizeof(double) : sizeof(float);
     int reach[3] = {0, 0, 0};
-    if (match_set<D3Q39>(lat, c->perm)) {
+    double w1[kMaxQ1] = {0.0};
+    const bool tensor = match_tensor<D1Q9P1>(lat, c->perm, w1);
+    if (tensor) {
+        c->kind = 2;
+        c->np = 0;
+        for (int k = 0; k < 3; ++k) reach[k] = D1Q9P1::E(D1Q9P1::NP1 - 1);
+        c->ks = prec == LB_F64 ? kernels_d3q729_p0(N) : (prec == LB_F32 ? kernels_d3q729_p1(N) : nullptr);
+        c->as = nullptr;
+        // batched 1D lines only, shifted along x only
+        if (grid->ny != 1 || grid->nz != 1 || lat->shift[1] != 0 || lat->shift[2] != 0) c->ks = nullptr;
+    } else if (match_set<D3Q39>(lat, c->perm)) {
         c->kind = 0;
         c->np = D3Q39::NP;
         for (int k = 0; k < 3; ++k) reach[k] = max_reach<D3Q39>(k);
@@ -231,9 +276,13 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     CtxView &v = c->view;
     std::memset(&v, 0, sizeof(v));
     v.stream = static_cast<cudaStream_t>(stream);
-    for (int i = 0; i < c->q; ++i) v.plane[i] = (long long)c->perm[i] * (long long)c->stride;
-    v.wp[0] = lat->w[c->perm[0]];
-    for (int p = 0; p < c->np; ++p) v.wp[p + 1] = lat->w[c->perm[2 * p + 1]];
+    if (!tensor) {
+        for (int i = 0; i < c->q; ++i) v.plane[i] = (long long)c->perm[i] * (long long)c->stride;
+        v.wp[0] = lat->w[c->perm[0]];
+        for (int p = 0; p < c->np; ++p) v.wp[p + 1] = lat->w[c->perm[2 * p + 1]];
+    }
+    for (int k = 0; k < kMaxQ1; ++k) v.w1[k] = w1[k];
+    v.stride = (long long)c->stride;
     v.c = lat->c;
     v.nx = line ? c->nx_inst[0] : grid->nx;
     v.ny = grid->ny;
@@ -250,6 +299,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&c->d_inst, sizeof(InstanceInfo) * grid->batch);
     if (e == cudaSuccess && line) e = cudaMalloc(&c->d_tiles, sizeof(int2) * c->max_tiles);
+    if (e == cudaSuccess && tensor) e = cudaMalloc(&c->d_plane, sizeof(int) * c->q);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghosts, c->elem * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghostsd, sizeof(double) * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_states, sizeof(double) * 10 * grid->batch);
@@ -269,6 +319,8 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     }
     if (!tiles.empty())
         e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, v.stream);
+    if (e == cudaSuccess && tensor)
+        e = cudaMemcpyAsync(c->d_plane, c->perm.data(), sizeof(int) * c->q, cudaMemcpyHostToDevice, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_health, 0, 16, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ghosts, 0, c->elem * c->q * 2 * grid->batch, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ghostsd, 0, sizeof(double) * c->q * 2 * grid->batch, v.stream);
@@ -283,6 +335,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     }
     v.inst = c->d_inst;
     v.tiles = c->d_tiles;
+    v.plane_idx = c->d_plane;
     v.ghosts = c->d_ghosts;
     v.ghostsd = c->d_ghostsd;
     v.health = c->d_health;

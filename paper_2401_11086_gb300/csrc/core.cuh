@@ -158,6 +158,26 @@ SMRT_HD void maxwell_divided(T (&G)[N + 1], T u, T thm1) {
     });
 }
 
+// a4 in divided form: td_beta = d_beta / beta! = theta^(-|beta|/2) [T(-u, 2 - theta) ta]_beta,
+// v holding ta on entry (with the full a_0 = rho in slot 0) and td on exit.
+template <int Nm, class T>
+SMRT_D void to_local_divided(T (&v)[nmom(Nm)], const T (&u)[3], T theta, T thm1) {
+    T G[3][Nm + 1];
+    static_for<3>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        maxwell_divided<Nm, T>(G[k], -u[k], -thm1);
+    });
+    binomial_divided<Nm, T>(v, G);
+    const T is = rsq(theta);
+    T sp[Nm + 1];
+    sp[0] = T(1);
+    static_for<Nm>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * is; });
+    static_for<nmom(Nm)>([&](auto A) {
+        constexpr int p = decltype(A)::value;
+        if constexpr (mi_order(p) >= 1) v[p] *= sp[mi_order(p)];
+    });
+}
+
 // ------------------------------------------------------------------ irreducible relaxation
 // Appendix A: the part of order n with m traces is P_m d = B(n,m) Q^(n-2m)_0 tr^m d delta^m,
 // Q^(r)_0 = sum_k D(r,k) delta^k tr^k. Collecting terms with j = m + k traces gives

@@ -5,10 +5,12 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "tensor.cuh"
 
 namespace smrt {
 
-constexpr int kMaxQ = 103;
+constexpr int kMaxQ = 103;   // largest set with a per-population plane table in the launch
+constexpr int kMaxQTP = 729; // largest tensor-product set (plane table in device memory)
 constexpr int kMaxNP = 51;
 constexpr int kTile = 128;  // cells per block (threads per block) for every kernel
 
@@ -32,6 +34,11 @@ struct CtxView {
     unsigned step;   // launch counter of lb_step (seeds the stochastic rounding)
     int tile_width;  // cells (threads) per block of the line kernels: 32, 64 or 128
     unsigned *bar;   // persistent launch: arrival count, generation, step counter
+    // tensor-product sets (D3Q729): caller plane of each library population (device table),
+    // the plane stride, and the 1D weights in library order
+    const int *plane_idx;
+    long long stride;
+    double w1[kMaxQ1];
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
@@ -54,8 +61,6 @@ struct KernelSet {
 };
 
 // precision: 0 double, 1 float, 2 float with double conserved sums and equilibrium rebuild
-const KernelSet *kernels_d3q39(int N, int precision);
-const KernelSet *kernels_d3q103(int N, int precision);
 
 template <class Lat, class T>
 StepArgs<Lat, T> make_args(const CtxView &v, const void *fin, void *fout) {
@@ -181,6 +186,96 @@ const KernelSet *kernel_set() {
                                  &launch_fill<Lat, N, T>, &launch_ghost<Lat, N, T>,
                                  &launch_persistent<Lat, N, T, Acc, Split>,
                                  &persistent_occupancy<Lat, N, T, Acc, Split>};
+    return &ks;
+}
+
+// ------------------------------------------------------------------ tensor-product sets
+template <class T>
+TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
+    TPArgs<T> a;
+    a.fin = static_cast<const T *>(fin);
+    a.fout = static_cast<T *>(fout);
+    a.inst = v.inst;
+    a.tiles = v.tiles;
+    a.ghosts = static_cast<const T *>(v.ghosts);
+    a.ghostsd = v.ghostsd;
+    a.health = v.health;
+    a.plane_idx = v.plane_idx;
+    a.stride = v.stride;
+    for (int k = 0; k < kMaxQ1; ++k) a.w1[k] = v.w1[k];
+    a.cd = v.c;
+    a.step = v.step;
+    return a;
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
+    const TPArgs<T> a = make_tp_args<T>(v, fin, fout);
+    if (v.fixedx)
+        tp_step_line_kernel<L1, N, T, true><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
+    else
+        tp_step_line_kernel<L1, N, T, false><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_moments(const CtxView &v, const void *f, double *out, unsigned mask) {
+    const TPArgs<T> a = make_tp_args<T>(v, f, nullptr);
+    tp_moments_kernel<L1, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(a, out, v.ncells, mask, v.fixedx);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_fill(const CtxView &v, void *f, const double *rho, const double *u, const double *theta) {
+    const TPArgs<T> a = make_tp_args<T>(v, nullptr, f);
+    tp_fill_kernel<L1, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(a, rho, u, theta, v.ncells);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_ghost(const CtxView &v, const double *states, int ninst, void *ghosts, double *ghostsd) {
+    const TPArgs<T> a = make_tp_args<T>(v, nullptr, nullptr);
+    const int n = 2 * ninst;
+    tp_ghost_kernel<L1, N, T><<<(n + 63) / 64, 64, 0, v.stream>>>(a, states, ninst, static_cast<T *>(ghosts), ghostsd);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, int grid) {
+    const TPArgs<T> a = make_tp_args<T>(v, fa, fb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(v.tile_width);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = v.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int ntiles = v.ntiles;
+    unsigned *bar = v.bar;
+    if (v.fixedx)
+        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent<L1, N, T, true>, a, nsteps, ntiles, bar);
+    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent<L1, N, T, false>, a, nsteps, ntiles, bar);
+}
+
+template <class L1, int N, class T>
+int tp_persistent_occupancy(const CtxView &v) {
+    int n = 0;
+    const cudaError_t e =
+        v.fixedx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent<L1, N, T, true>, v.tile_width, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent<L1, N, T, false>, v.tile_width, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+// P: 0 double, 1 float (the split precision has no tensor-product kernel)
+template <class L1, int N, int P>
+const KernelSet *tp_kernel_set() {
+    using T = typename std::conditional<P == 0, double, float>::type;
+    static const KernelSet ks = {&tp_launch_step<L1, N, T>,       &tp_launch_moments<L1, N, T>,
+                                 &tp_launch_fill<L1, N, T>,       &tp_launch_ghost<L1, N, T>,
+                                 &tp_launch_persistent<L1, N, T>, &tp_persistent_occupancy<L1, N, T>};
     return &ks;
 }
 

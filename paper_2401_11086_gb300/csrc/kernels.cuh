@@ -204,20 +204,7 @@ struct Collide {
     // a4: td_beta = d_beta / beta! = theta^(-|beta|/2) [T(-u, 2 - theta) ta]_beta
     template <int Nm>
     SMRT_D static void to_local(T (&v)[nmom(Nm)], const T (&u)[3], T theta, T thm1) {
-        T G[3][Nm + 1];
-        static_for<3>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            maxwell_divided<Nm, T>(G[k], -u[k], -thm1);
-        });
-        binomial_divided<Nm, T>(v, G);
-        const T is = rsq(theta);
-        T sp[Nm + 1];
-        sp[0] = T(1);
-        static_for<Nm>([&](auto J) { sp[decltype(J)::value + 1] = sp[decltype(J)::value] * is; });
-        static_for<nmom(Nm)>([&](auto A) {
-            constexpr int p = decltype(A)::value;
-            if constexpr (mi_order(p) >= 1) v[p] *= sp[mi_order(p)];
-        });
+        to_local_divided<Nm, T>(v, u, theta, thm1);
     }
 
     // a7 + a8 helper: values f'_i = w_i sum_gamma P_gamma e_i^gamma with
@@ -584,6 +571,50 @@ __global__ void __launch_bounds__(128) step_line_persistent(StepArgs<Lat, T> a, 
 }
 
 // ------------------------------------------------------------------------------ moments
+// The rows of lb_moments selected by mask, for one cell: rho, the physical velocity up,
+// theta, and the local-frame coefficients in divided form v (td_beta = d_beta / beta!,
+// |beta| <= Nm) of the pulled (pre-collision) populations.
+template <int Nm, class T>
+SMRT_D void store_moments(double *o, long long nc, long long cell, unsigned mask, double rho,
+                          const double (&up)[3], double thd, const T (&v)[nmom(Nm)]) {
+    constexpr int Mm = nmom(Nm);
+    // undivide: d_beta = beta! td_beta
+    double d[Mm];
+    static_for<Mm>([&](auto A) {
+        constexpr int p = decltype(A)::value;
+        d[p] = double(v[p]) * mi_fact(p);
+    });
+    d[0] = rho;
+    long long r = 0;
+    if (mask & 0x1u) o[(r++) * nc + cell] = rho;
+    if (mask & 0x2u) {
+        o[(r++) * nc + cell] = up[0];
+        o[(r++) * nc + cell] = up[1];
+        o[(r++) * nc + cell] = up[2];
+    }
+    if (mask & 0x4u) o[(r++) * nc + cell] = thd;
+    if (mask & 0x8u) {
+        o[(r++) * nc + cell] = thd * d[mi_pos(2, 0, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 2, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 0, 2)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(1, 1, 0)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(1, 0, 1)];
+        o[(r++) * nc + cell] = thd * d[mi_pos(0, 1, 1)];
+    }
+    if (mask & 0x10u) {
+        const double s = 0.5 * thd * sqrt(thd);
+        o[(r++) * nc + cell] = s * (d[mi_pos(3, 0, 0)] + d[mi_pos(1, 2, 0)] + d[mi_pos(1, 0, 2)]);
+        o[(r++) * nc + cell] = s * (d[mi_pos(2, 1, 0)] + d[mi_pos(0, 3, 0)] + d[mi_pos(0, 1, 2)]);
+        o[(r++) * nc + cell] = s * (d[mi_pos(2, 0, 1)] + d[mi_pos(0, 2, 1)] + d[mi_pos(0, 0, 3)]);
+    }
+    if (mask & 0x20u) {
+        static_for<Mm>([&](auto A) {
+            constexpr int p = decltype(A)::value;
+            o[(r + p) * nc + cell] = d[p];
+        });
+    }
+}
+
 // Moments of the pulled (pre-collision) populations; see lb_moments in smrt.h.
 template <class Lat, int N, class T, class Acc>
 struct MomentArgs {
@@ -665,44 +696,8 @@ __global__ void __launch_bounds__(128) moments_kernel(MomentArgs<Lat, N, T, Acc>
     v[0] = T(rho);
     const T ut[3] = {T(u[0]), T(u[1]), T(u[2])};
     Cm::template to_local<Nm>(v, ut, T(th), T(thm1));
-    // undivide: d_beta = beta! td_beta
-    double d[Mm];
-    static_for<Mm>([&](auto A) {
-        constexpr int p = decltype(A)::value;
-        d[p] = double(v[p]) * mi_fact(p);
-    });
-    d[0] = double(rho);
-    const double thd = double(th);
-    double *o = m.out;
-    const long long nc = m.ncells;
-    long long r = 0;
-    if (m.mask & 0x1u) o[(r++) * nc + cell] = double(rho);
-    if (m.mask & 0x2u) {
-        o[(r++) * nc + cell] = double(u[0]) + ubar_x;
-        o[(r++) * nc + cell] = double(u[1]) + a.cd * a.ky;
-        o[(r++) * nc + cell] = double(u[2]) + a.cd * a.kz;
-    }
-    if (m.mask & 0x4u) o[(r++) * nc + cell] = thd;
-    if (m.mask & 0x8u) {
-        o[(r++) * nc + cell] = thd * d[mi_pos(2, 0, 0)];
-        o[(r++) * nc + cell] = thd * d[mi_pos(0, 2, 0)];
-        o[(r++) * nc + cell] = thd * d[mi_pos(0, 0, 2)];
-        o[(r++) * nc + cell] = thd * d[mi_pos(1, 1, 0)];
-        o[(r++) * nc + cell] = thd * d[mi_pos(1, 0, 1)];
-        o[(r++) * nc + cell] = thd * d[mi_pos(0, 1, 1)];
-    }
-    if (m.mask & 0x10u) {
-        const double s = 0.5 * thd * sqrt(thd);
-        o[(r++) * nc + cell] = s * (d[mi_pos(3, 0, 0)] + d[mi_pos(1, 2, 0)] + d[mi_pos(1, 0, 2)]);
-        o[(r++) * nc + cell] = s * (d[mi_pos(2, 1, 0)] + d[mi_pos(0, 3, 0)] + d[mi_pos(0, 1, 2)]);
-        o[(r++) * nc + cell] = s * (d[mi_pos(2, 0, 1)] + d[mi_pos(0, 2, 1)] + d[mi_pos(0, 0, 3)]);
-    }
-    if (m.mask & 0x20u) {
-        static_for<Mm>([&](auto A) {
-            constexpr int p = decltype(A)::value;
-            o[(r + p) * nc + cell] = d[p];
-        });
-    }
+    const double up[3] = {double(u[0]) + ubar_x, double(u[1]) + a.cd * a.ky, double(u[2]) + a.cd * a.kz};
+    store_moments<Nm, T>(m.out, m.ncells, cell, m.mask, double(rho), up, double(th), v);
 }
 
 // ------------------------------------------------------------------------------ equilibrium

@@ -17,6 +17,7 @@
 
 #include "../../include/smrt.h"
 #include "lattices.cuh"
+#include "tensor.cuh"
 
 namespace smrt {
 
@@ -197,6 +198,95 @@ double quadrature_defect(int q, const int8_t *e, const double *w, double c, int 
     return worst;
 }
 
+// 1D rule on c {0, +-E_0, .., +-E_{NP1-1}} (Sec. 4.2, D1Qd-P1): rest weight W_0 and pair
+// weights W_1..W_NP1 from the even-moment conditions sum_i w_i (c e_i)^(2m) = (2m - 1)!!,
+// m = 0..NP1, at fixed c (NP1 + 1 linear equations); the remaining condition, m = NP1 + 1,
+// fixes c by bracketing and bisection, as for the cubic sets.
+template <class L1>
+static bool weights_1d(long double c, std::vector<long double> &W, long double &resid) {
+    const int S = L1::NP1 + 1;
+    auto mom = [&](int s, int a) -> long double {
+        if (s == 0) return a == 0 ? 1.0L : 0.0L;
+        return 2.0L * powl(c * L1::E(s - 1), a);
+    };
+    std::vector<long double> A(S * S), b(S);
+    for (int r = 0; r < S; ++r) {
+        for (int s = 0; s < S; ++s) A[r * S + s] = mom(s, 2 * r);
+        b[r] = gauss_moment(2 * r);
+    }
+    if (!solve_linear(A, b, S, W)) return false;
+    long double v = 0.0L;
+    for (int s = 0; s < S; ++s) v += W[s] * mom(s, 2 * S);
+    resid = v - gauss_moment(2 * S);
+    return 2 * S + 1 == L1::DEGREE;
+}
+
+template <class L1>
+static bool solve_rule_1d(double &c_out, std::vector<double> &w_out) {
+    const long double c0 = L1::C_GUESS;
+    const int steps = 400;
+    std::vector<long double> W;
+    long double prev_c = c0 * 0.9L, prev_r;
+    if (!weights_1d<L1>(prev_c, W, prev_r)) return false;
+    bool have = false;
+    long double best_c = 0.0L;
+    std::vector<long double> best_W;
+    for (int k = 1; k <= steps; ++k) {
+        const long double cc = c0 * (0.9L + 0.2L * k / steps);
+        long double r;
+        if (!weights_1d<L1>(cc, W, r)) return false;
+        if ((r < 0) != (prev_r < 0)) {
+            long double lo = prev_c, hi = cc, rlo = prev_r, rm = 0.0L;
+            for (int it = 0; it < 200; ++it) {
+                const long double mid = 0.5L * (lo + hi);
+                weights_1d<L1>(mid, W, rm);
+                if ((rm < 0) == (rlo < 0))
+                    lo = mid, rlo = rm;
+                else
+                    hi = mid;
+            }
+            const long double cm = 0.5L * (lo + hi);
+            weights_1d<L1>(cm, W, rm);
+            bool positive = true;
+            for (long double wv : W) positive = positive && (wv > 0.0L);
+            if (fabsl(rm) < 1e-9L && positive && (!have || fabsl(cm - c0) < fabsl(best_c - c0))) {
+                have = true;
+                best_c = cm;
+                best_W = W;
+            }
+        }
+        prev_c = cc, prev_r = r;
+    }
+    if (!have) return false;
+    c_out = (double)best_c;
+    w_out.assign(L1::Q1, 0.0);  // library order: rest, then +E_p, -E_p
+    w_out[0] = (double)best_W[0];
+    for (int p = 0; p < L1::NP1; ++p) w_out[2 * p + 1] = w_out[2 * p + 2] = (double)best_W[p + 1];
+    return true;
+}
+
+// The 3D tensor product of a 1D rule in library order i = a + d b + d^2 c.
+template <class L1>
+static lb_status named_tensor(int8_t *e_out, double *w_out, double *c_out, int *q_out, int *deg_out,
+                              int capacity) {
+    constexpr int Q1 = L1::Q1, Q = Q1 * Q1 * Q1;
+    if (capacity < Q) return LB_ERR_INVALID;
+    double c;
+    std::vector<double> w1;
+    if (!solve_rule_1d<L1>(c, w1)) return LB_ERR_INVALID;
+    for (int i = 0; i < Q; ++i) {
+        const int a = i % Q1, b = (i / Q1) % Q1, cc = i / (Q1 * Q1);
+        e_out[3 * i] = (int8_t)e1<L1>(a);
+        e_out[3 * i + 1] = (int8_t)e1<L1>(b);
+        e_out[3 * i + 2] = (int8_t)e1<L1>(cc);
+        w_out[i] = w1[a] * w1[b] * w1[cc];
+    }
+    *c_out = c;
+    *q_out = Q;
+    *deg_out = L1::DEGREE;
+    return LB_OK;
+}
+
 }  // namespace smrt
 
 extern "C" lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w_out, double *c_out,
@@ -206,6 +296,8 @@ extern "C" lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w
         return smrt::named<smrt::D3Q39>(e_out, w_out, c_out, q_out, degree_out, capacity);
     if (std::strcmp(name, "D3Q103") == 0)
         return smrt::named<smrt::D3Q103>(e_out, w_out, c_out, q_out, degree_out, capacity);
+    if (std::strcmp(name, "D3Q729") == 0)
+        return smrt::named_tensor<smrt::D1Q9P1>(e_out, w_out, c_out, q_out, degree_out, capacity);
     return LB_ERR_INVALID;
 }
 

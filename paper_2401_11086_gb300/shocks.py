@@ -23,10 +23,19 @@ GAMMA = 5.0 / 3.0
 MA_STABLE_DEGREE9 = 3.0
 
 # Table 4: tau*_{n,m} = tau_{n,m} / tau_{2,0}, Maxwell molecules (SMRT) and the Shakhov model,
-# in lb_set_relaxation's order (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2). tau_{2,1} (bulk) is
-# absent for a monatomic gas; its mode vanishes identically, 1 is used.
-TAU_RATIOS_SMRT = (1.0, 1.0, 2.0 / 3.0, 3.0 / 2.0, 432.0 / 763.0, 6.0 / 7.0, 3.0 / 2.0)
-TAU_RATIOS_SHAKHOV = (1.0, 1.0, 1.0, 3.0 / 2.0, 1.0, 1.0, 1.0)
+# in lb_set_relaxation's order (2,0) (2,1) (3,0) (3,1) (4,0) (4,1) (4,2) (5,0) (5,1) (5,2).
+# tau_{2,1} (bulk) is absent for a monatomic gas; its mode vanishes identically, 1 is used.
+TAU_RATIOS_SMRT = (1.0, 1.0, 2.0 / 3.0, 3.0 / 2.0, 432.0 / 763.0, 6.0 / 7.0, 3.0 / 2.0,
+                   864.0 / 1655.0, 108.0 / 163.0, 1.0)
+TAU_RATIOS_SHAKHOV = (1.0, 1.0, 1.0, 3.0 / 2.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+# Sec. 4.3's "reduced" operator: the SMRT table with tau*_{4,1} = tau*_{4,2} = 6/7, so that the
+# two traced parts of the order-4 tensor relax together.
+TAU_RATIOS_REDUCED = (1.0, 1.0, 2.0 / 3.0, 3.0 / 2.0, 432.0 / 763.0, 6.0 / 7.0, 6.0 / 7.0,
+                      864.0 / 1655.0, 108.0 / 163.0, 1.0)
+
+# Table 3: reference temperature (upstream theta1) of the paper's runs on the D1Q9-P1 product
+# set, by upstream Mach number; the frame shift is k_x = 2 in every row.
+TABLE3_THETA1 = {1.5: 0.714, 3.0: 0.333, 5.0: 0.167}
 
 
 def ntau(N: int) -> int:
@@ -34,9 +43,15 @@ def ntau(N: int) -> int:
 
 
 def shock_params(Ma: float, c: float, N: int, ell_cells: float = 2.0, ratios=TAU_RATIOS_SMRT,
-                 theta2_max: float = 1.2):
-    """End states, frame shift and continuous relaxation times of one shock."""
-    theta1, kx = api.lb_shock_frame(Ma, c, GAMMA, theta2_max)
+                 theta2_max: float = 1.2, theta1: float | None = None):
+    """End states, frame shift and continuous relaxation times of one shock. theta1 overrides
+    the reference temperature (e.g. a Table 3 value); the frame shift follows it."""
+    t1, kx = api.lb_shock_frame(Ma, c, GAMMA, theta2_max)
+    if theta1 is not None and theta1 != t1:
+        # k = round(((u1 + u2) / 2) / c) with the given upstream temperature
+        mean = (GAMMA * Ma * Ma + 1.0) / ((GAMMA + 1.0) * Ma) * np.sqrt(GAMMA * theta1)
+        t1, kx = theta1, int(np.floor(mean / c + 0.5))
+    theta1 = t1
     left, right = api.lb_rankine_hugoniot(Ma, GAMMA, 1.0, theta1)
     tau20 = ell_cells * c / np.sqrt(theta1)
     taus = [r * tau20 for r in ratios[: ntau(N)]]
@@ -44,9 +59,13 @@ def shock_params(Ma: float, c: float, N: int, ell_cells: float = 2.0, ratios=TAU
 
 
 def tanh_fields(params, L: int, width: float):
-    """rho, u_x, theta of the tanh blend between the end states (x0 = L/2)."""
+    """rho, u_x, theta of the tanh blend between the end states (x0 = L/2); width <= 0 gives
+    the step of the paper's runs (Sec. 4.2): upstream on x < L/2, downstream beyond."""
     x = np.arange(L, dtype=np.float64)
-    s = 0.5 * (1.0 + np.tanh((x - L / 2.0) / width))
+    if width > 0:
+        s = 0.5 * (1.0 + np.tanh((x - L / 2.0) / width))
+    else:
+        s = (x >= L // 2).astype(np.float64)
     lf, rt = params["left"], params["right"]
     rho = lf["rho"] + (rt["rho"] - lf["rho"]) * s
     u = lf["u"][0] + (rt["u"][0] - lf["u"][0]) * s
@@ -55,11 +74,13 @@ def tanh_fields(params, L: int, width: float):
 
 
 def setup_batch(lattice: api.LatticeDesc, N: int, machs, lengths, precision: str = "f32c64",
-                ell_cells: float = 2.0, width: float = 10.0, stream=None):
+                ell_cells: float = 2.0, width: float = 10.0, stream=None, ratios=TAU_RATIOS_SMRT,
+                theta1=None):
     """A batched context with one shock per (Ma, L) and its initial state: the equilibrium of
     the tanh blend of width `width` cells (10 by default: a wider blend puts intermediate
     (u, theta) states into the cells that, above Ma ~ 3.5, leave the stable range of a degree-9
-    velocity set). Returns (ctx, state, per-instance params)."""
+    velocity set; width <= 0: a step). ratios: tau*_{n,m} table; theta1: optional per-instance
+    upstream temperatures (e.g. Table 3's). Returns (ctx, state, per-instance params)."""
     import torch
     lat = api.LatticeDesc(lattice.e, lattice.w, lattice.c, lattice.degree, (0, 0, 0))
     ctx = api.lb_init_lattice(lat, 0, N=N, precision=precision, bc_x=1,
@@ -67,7 +88,8 @@ def setup_batch(lattice: api.LatticeDesc, N: int, machs, lengths, precision: str
     params = []
     rho, ux, th = [], [], []
     for j, (Ma, L) in enumerate(zip(machs, lengths)):
-        p = shock_params(float(Ma), lattice.c, N, ell_cells)
+        t1 = None if theta1 is None else float(theta1[j])
+        p = shock_params(float(Ma), lattice.c, N, ell_cells, ratios=ratios, theta1=t1)
         api.lb_set_frame_shift(ctx, j, p["kx"])
         api.lb_set_relaxation(ctx, p["taus"], True, 1.0, p["left"], p["right"], instance=j)
         r, u, t = tanh_fields(p, int(L), width)

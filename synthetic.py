@@ -28,6 +28,12 @@ def tanh_blend(L: int, width: float, q1: float, q2: float, x0: float | None = No
     return q1 + (q2 - q1) * 0.5 * (1.0 + np.tanh((x - x0) / width))
 
 
+def step_blend(L: int, q1: float, q2: float) -> np.ndarray:
+    """The initial condition of the paper's shock runs (Sec. 4.2): q1 on x < L/2, q2 beyond."""
+    x = np.arange(L)
+    return np.where(x < L // 2, q1, q2).astype(np.float64)
+
+
 def taylor_green(n: int, amplitude: float = 0.05, noise: float = 1e-3, seed: int = SEED,
                  shape: tuple | None = None):
     """Fields on an (nz, ny, nx) grid (default n^3): rho (noisy), u (3, ...), theta."""

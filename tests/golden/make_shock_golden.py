@@ -5,6 +5,7 @@ touches the CUDA path. Usage:
 
     python tests/golden/make_shock_golden.py ma3_d3q103_n4          # Ma = 3, 2048 cells, 20000 steps
     python tests/golden/make_shock_golden.py ma5_d3q103_n4_target   # Ma = 5, 1024 cells, 5000 steps
+    python tests/golden/make_shock_golden.py ma3_d3q729_n5          # Table 3 row Ma = 3, 100 cells
 
 Each case stores, at the listed step counts, the moments of the pre-collision populations
 (rho, physical u_x, theta, q_x) on every cell, float64.
@@ -32,18 +33,24 @@ CASES = {
     # target of the differentiable shock: Ma = 5, 1024 cells, Table 4 times, 5000 steps
     "ma5_d3q103_n4_target": dict(lattice="D3Q103", N=4, Ma=5.0, nx=1024, width=10.0,
                                  checkpoints=(5000,)),
+    # the paper's own configuration (Sec. 4.2, Table 3 row Ma = 3): D3Q729, N = 5, 100 cells,
+    # theta1 = 0.333, k_x = 2, step initial condition, Table 4 SMRT times, ell = 2 cells
+    "ma3_d3q729_n5": dict(lattice="D3Q729", N=5, Ma=3.0, nx=100, width=0.0, theta1=0.333,
+                          checkpoints=(200, 1000)),
 }
 
 
 def run(name: str):
     cfg = CASES[name]
     lat = L.by_name(cfg["lattice"])
-    case = K.shock_case(lat, cfg["N"], cfg["Ma"], cfg["nx"])
+    case = K.shock_case(lat, cfg["N"], cfg["Ma"], cfg["nx"], theta1=cfg.get("theta1"))
     st = case.states
     nx, W = cfg["nx"], cfg["width"]
-    h = K.initial_state(case, synthetic.tanh_blend(nx, W, st["rho1"], st["rho2"]),
-                        synthetic.tanh_blend(nx, W, st["u1"], st["u2"]),
-                        synthetic.tanh_blend(nx, W, st["theta1"], st["theta2"]))
+    if W > 0:
+        prof = lambda k: synthetic.tanh_blend(nx, W, st[k + "1"], st[k + "2"])  # noqa: E731
+    else:
+        prof = lambda k: synthetic.step_blend(nx, st[k + "1"], st[k + "2"])  # noqa: E731
+    h = K.initial_state(case, prof("rho"), prof("u"), prof("theta"))
     out = {"theta1": case.theta1, "k": case.k, "tau_ref": case.model.tau_ref}
     t0 = time.time()
     done = 0

@@ -43,7 +43,7 @@ def test_error_strings(lib):
     assert lib.lb_error_string(99) == b"unknown status"
 
 
-@pytest.mark.parametrize("name", ["D3Q39", "D3Q103"])
+@pytest.mark.parametrize("name", ["D3Q39", "D3Q103", "D3Q729"])
 def test_library_lattice_agrees_with_oracle(lib, name):
     import paper_2401_11086_gb300 as P
     d = P.lb_lattice_named(name)
@@ -97,10 +97,18 @@ def test_validation_before_any_cuda_call(lib):
 
 
 def test_unknown_lattice_is_unsupported(lib):
-    """A valid degree-11 rule the library has no kernel for (the paper's D3Q729)."""
+    """Requests the library has no kernel for are refused before any CUDA call."""
+    import paper_2401_11086_gb300 as P
     o = OL.d3q729()
-    assert _init(lib, o.e[:103], o.w[:103], o.c, 11) in (1, 5)
+    assert _init(lib, o.e[:103], o.w[:103], o.c, 11) == 1        # not a quadrature
     assert lib.lb_lattice_named(b"D3Q729", None, None, None, None, None, 0) == 1
+    d = P.lb_lattice_named("D3Q729")
+    # the tensor-product set: 1D lines only, N = 4 or 5, double or float
+    assert _init(lib, d.e, d.w, d.c, 11, N=5, prec=0) == 5       # 8^3 box
+    assert _init(lib, d.e, d.w, d.c, 11, N=3, prec=0, nx=100, ny=1, nz=1) == 5
+    assert _init(lib, d.e, d.w, d.c, 11, N=5, prec=2, nx=100, ny=1, nz=1) == 5
+    assert _init(lib, d.e, d.w, d.c, 11, N=5, prec=0, nx=100, ny=1, nz=1, shift=(2, 1, 0)) == 5
+    assert _init(lib, d.e, d.w, d.c, 11, N=6, prec=0, nx=100, ny=1, nz=1) == 1  # degree < 2N
 
 
 @pytest.mark.parametrize("Ma", [1.2, 1.5, 1.9, 3.0, 5.0, 7.0])

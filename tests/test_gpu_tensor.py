@@ -1,0 +1,225 @@
+"""Parity of the tensor-product kernels (D3Q729 = D1Q9-P1^3, N = 4 and 5: the paper's own
+configuration, Sec. 4.2 / Table 3) with the FP64 oracle, through the C ABI.
+
+Every expected value comes from ``oracle/`` or from a golden file written by
+tests/golden/make_shock_golden.py (oracle only). FP64 kernels agree with the oracle to
+round-off (1e-11 relative to the population scale); FP32 kernels to 2e-6 per step.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import lattice as OL
+from oracle import shock as OK
+from oracle import smrt as OS
+from _lb import download, lib_from_oracle, upload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2401_11086_gb300 as P  # noqa: E402
+from paper_2401_11086_gb300 import shocks  # noqa: E402
+
+# Table 3 rows on the D1Q9-P1 product set, ragged lengths (several 32/64/128-cell tiles)
+MACHS = [1.5, 3.0, 5.0]
+LENGTHS = [100, 37, 150]
+
+
+@pytest.fixture(scope="module")
+def lat():
+    o = OL.d3q729()
+    d = P.lb_lattice_named("D3Q729")
+    return o, d, lib_from_oracle(o, d)
+
+
+def _desc(d, shift):
+    return P.LatticeDesc(e=d.e, w=d.w, c=d.c, degree=d.degree, shift=tuple(shift))
+
+
+def _tau(model):
+    keys = [(n, m) for n in range(2, model.N + 1) for m in range(n // 2 + 1)]
+    return [model.tau_star[k] * model.tau_ref for k in keys]
+
+
+def _oracle_case(olat, N, Ma, L, tau_star=None):
+    case = OK.shock_case(olat, N, Ma, L, theta1=shocks.TABLE3_THETA1[Ma], tau_star=tau_star)
+    st = case.states
+    h = OK.initial_state(case, *[synthetic.step_blend(L, st[k + "1"], st[k + "2"])
+                                 for k in ("rho", "u", "theta")])
+    return case, h
+
+
+def _upload_batch(ctx, d, idx, hs):
+    flat = np.concatenate([h.reshape(h.shape[0], -1) for h in hs], axis=1)
+    st = ctx.new_state()
+    ctx.planes(st)[:] = torch.from_numpy(np.ascontiguousarray(flat[idx] - d.w[:, None])).to(ctx.device, ctx.dtype)
+    return st
+
+
+def _download_batch(ctx, d, idx, st, lengths):
+    arr = ctx.planes(st).double().cpu().numpy() + d.w[:, None]
+    out = np.empty_like(arr)
+    out[idx] = arr
+    offs = np.concatenate([[0], np.cumsum(lengths)])
+    return [out[:, offs[j]:offs[j + 1]] for j in range(len(lengths))]
+
+
+def _batch(olat, d, N, prec, tau_star=None, ratios=shocks.TAU_RATIOS_SMRT):
+    ctx, _, params = shocks.setup_batch(d, N, MACHS, LENGTHS, precision=prec, width=0.0,
+                                        ratios=ratios, theta1=[shocks.TABLE3_THETA1[m] for m in MACHS])
+    cases, hs = zip(*[_oracle_case(olat, N, Ma, L, tau_star) for Ma, L in zip(MACHS, LENGTHS)])
+    return ctx, params, list(cases), list(hs)
+
+
+@pytest.mark.parametrize("N", [4, 5])
+@pytest.mark.parametrize("table", ["smrt", "shakhov", "reduced"])
+def test_table3_shocks_match_oracle(lat, N, table):
+    """FP64, the three Table 3 rows (Ma 1.5/3/5, theta1 = 0.714/0.333/0.167, k_x = 2) in one
+    batch from the step initial condition, 12 steps, each instance vs its own oracle run;
+    SMRT, Shakhov and the 'reduced' tau_41 = tau_42 table of Sec. 4.3."""
+    olat, d, idx = lat
+    star = {"smrt": OS.TAU_STAR_SMRT, "shakhov": OS.TAU_STAR_SHAKHOV,
+            "reduced": {**OS.TAU_STAR_SMRT, (4, 2): 6.0 / 7.0}}[table]
+    ratios = {"smrt": shocks.TAU_RATIOS_SMRT, "shakhov": shocks.TAU_RATIOS_SHAKHOV,
+              "reduced": shocks.TAU_RATIOS_REDUCED}[table]
+    ctx, params, cases, hs = _batch(olat, d, N, "f64", star, ratios)
+    for p, case in zip(params, cases):
+        assert p["kx"] == case.k == 2
+        np.testing.assert_allclose(p["taus"], _tau(case.model), rtol=1e-14)
+    fa = _upload_batch(ctx, d, idx, hs)
+    nsteps = 12
+    out = P.lb_step(ctx, fa, ctx.new_state(), nsteps)
+    assert P.lb_poll_status(ctx)[0] == 0
+    got = _download_batch(ctx, d, idx, out, LENGTHS)
+    for j, (case, h) in enumerate(zip(cases, hs)):
+        for _ in range(nsteps):
+            h = OS.step(h, case.model, case.geom)
+        want = h.reshape(olat.q, -1)
+        assert np.abs(got[j] - want).max() / np.abs(want).max() < 1e-11, (j, MACHS[j])
+
+
+def test_fill_equilibrium_matches_oracle(lat):
+    olat, d, idx = lat
+    for prec, tol in (("f64", 1e-14), ("f32", 1e-7)):
+        ctx, f, params, = shocks.setup_batch(d, 5, MACHS, LENGTHS, precision=prec, width=0.0,
+                                             theta1=[shocks.TABLE3_THETA1[m] for m in MACHS])
+        got = _download_batch(ctx, d, idx, f, LENGTHS)
+        for j, (Ma, L) in enumerate(zip(MACHS, LENGTHS)):
+            _, h = _oracle_case(olat, 5, Ma, L)
+            want = h.reshape(olat.q, -1)
+            assert np.abs(got[j] - want).max() / np.abs(want).max() < tol
+
+
+def test_moments_match_oracle(lat):
+    """lb_moments (rho, u, theta, sigma, q and every local coefficient d up to order 5) of a
+    perturbed periodic line vs the oracle's macroscopic()."""
+    olat, d, idx = lat
+    nx, N = 90, 5
+    rho, u, th = synthetic.taylor_green(0, amplitude=0.1, noise=3e-3, seed=4, shape=(1, 1, nx))
+    f0 = OS.equilibrium(rho.ravel(), u.reshape(3, -1), th.ravel(), olat, N)
+    rng = np.random.default_rng(4)
+    f0 = (f0 * (1.0 + 0.05 * rng.standard_normal(f0.shape))).reshape(olat.q, 1, 1, nx)
+    shift = (2, 0, 0)
+    ctx = P.lb_init_lattice(_desc(d, shift), nx, N=N, precision="f64")
+    f = upload(ctx, f0, idx)
+    mask = P.LB_MOM_RHO | P.LB_MOM_U | P.LB_MOM_THETA | P.LB_MOM_SIGMA | P.LB_MOM_Q | P.LB_MOM_D
+    out = P.lb_moments(ctx, f, mask).cpu().numpy()
+    m = OS.macroscopic(f0, OS.Model(olat, N, tau_ref=1.0), OS.Geometry(shape=(1, 1, nx), shift=shift))
+    want = np.concatenate([m["rho"][None], m["u"], m["theta"][None], m["sigma"], m["q"], m["d"]])
+    assert out.shape == want.shape
+    np.testing.assert_allclose(out, want, rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_periodic_line_matches_oracle(lat, prec, tol):
+    """Periodic line of 133 cells (a ragged 5-cell tail), shift 2, perturbed populations,
+    1 and 4 steps."""
+    olat, d, idx = lat
+    nx, N = 133, 5
+    rho, u, th = synthetic.taylor_green(0, amplitude=0.08, noise=2e-3, seed=9, shape=(1, 1, nx))
+    f0 = OS.equilibrium(rho.ravel(), u.reshape(3, -1), th.ravel(), olat, N)
+    rng = np.random.default_rng(9)
+    f0 = (f0 * (1.0 + 0.02 * rng.standard_normal(f0.shape))).reshape(olat.q, 1, 1, nx)
+    shift = (2, 0, 0)
+    model = OS.Model(olat, N, tau_ref=0.7)
+    geom = OS.Geometry(shape=(1, 1, nx), shift=shift)
+    ctx = P.lb_init_lattice(_desc(d, shift), nx, N=N, precision=prec)
+    P.lb_set_relaxation(ctx, _tau(model), True, 1.0)
+    fa = upload(ctx, f0, idx)
+    h = download(ctx, fa, idx).reshape(f0.shape)     # start from the stored (rounded) state
+    for nsteps in (1, 4):
+        want = h
+        for _ in range(nsteps):
+            want = OS.step(want, model, geom)
+        got = download(ctx, P.lb_step(ctx, fa.clone(), ctx.new_state(), nsteps), idx)
+        assert np.abs(got - want.reshape(olat.q, -1)).max() / np.abs(want).max() < tol * nsteps
+
+
+def test_schedules_and_graph_are_bitwise_identical(lat):
+    """FP64: 12 steps under 32-, 64- and 128-cell tiles, the persistent cooperative launch and
+    its CUDA-graph replay give the same bits."""
+    olat, d, idx = lat
+    ctx, params, cases, hs = _batch(olat, d, 5, "f64")
+    f0 = _upload_batch(ctx, d, idx, hs)
+    runs = []
+    for mode, sched in [("step", (128, 0, 0)), ("step", (32, 0, 0)), ("step", (64, 0, 0)),
+                        ("step", (64, 1, 1)), ("graph", (32, 2, 1))]:
+        P.lb_set_schedule(ctx, *sched)
+        fa, fb = f0.clone(), ctx.new_state()
+        out = P.lb_step_graph(ctx, fa, fb, 12) if mode == "graph" else P.lb_step(ctx, fa, fb, 12)
+        assert P.lb_poll_status(ctx)[0] == 0
+        runs.append(out.clone())
+    for r in runs[1:]:
+        assert torch.equal(r, runs[0])
+
+
+def test_caller_velocity_order_is_free(lat):
+    """A context built on the oracle's own velocity order (any order is allowed) gives the
+    same populations as one in library order."""
+    olat, d, idx = lat
+    nx, N = 64, 4
+    case, h = _oracle_case(olat, N, 3.0, nx)
+    left, right = P.lb_rankine_hugoniot(3.0, theta1=case.theta1)
+    outs = []
+    for desc, order in ((_desc(d, (2, 0, 0)), idx),
+                        (P.LatticeDesc(e=olat.e.astype(np.int8), w=olat.w, c=olat.c, degree=11,
+                                       shift=(2, 0, 0)), np.arange(olat.q))):
+        ctx = P.lb_init_lattice(desc, nx, N=N, precision="f64", bc_x=1)
+        P.lb_set_relaxation(ctx, _tau(case.model), True, 1.0, left, right)
+        fa = upload(ctx, h, order)
+        outs.append(download(ctx, P.lb_step(ctx, fa, ctx.new_state(), 5), order))
+    want = h
+    for _ in range(5):
+        want = OS.step(want, case.model, case.geom)
+    for g in outs:
+        assert np.abs(g - want.reshape(olat.q, -1)).max() / np.abs(want).max() < 1e-11
+
+
+def test_paper_configuration_ma3_n5_against_golden(lat):
+    """The paper's Ma = 3 run (Table 3 row, D3Q729, N = 5, 100 cells, step start, SMRT
+    times), FP64, 1000 steps: moments vs the oracle's stored profiles."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "ma3_d3q729_n5.npz")
+    gold = np.load(path)
+    olat, d, idx = lat
+    ctx, f0, params = shocks.setup_batch(d, 5, [3.0], [100], precision="f64", width=0.0,
+                                         theta1=[0.333])
+    assert params[0]["kx"] == int(gold["k"])
+    np.testing.assert_allclose(params[0]["taus"][0], float(gold["tau_ref"]), rtol=1e-14)
+    mask = P.LB_MOM_RHO | P.LB_MOM_U | P.LB_MOM_THETA | P.LB_MOM_Q
+    fa, fb = f0, ctx.new_state()
+    done = 0
+    for cp in (200, 1000):
+        out = P.lb_step(ctx, fa, fb, cp - done)
+        fa, fb = out, (fb if out is fa else fa)
+        done = cp
+        assert P.lb_poll_status(ctx)[0] == 0
+        m = P.lb_moments(ctx, fa, mask).cpu().numpy()
+        assert np.abs(m[0] / gold[f"rho_{cp}"] - 1).max() < 1e-10
+        assert np.abs(m[1] - gold[f"u_{cp}"]).max() < 1e-10
+        assert np.abs(m[4] / gold[f"theta_{cp}"] - 1).max() < 1e-10
+        assert np.abs(m[5] - gold[f"q_{cp}"]).max() < 1e-10

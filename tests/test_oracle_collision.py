@@ -10,12 +10,12 @@ from oracle import smrt as S
 from oracle import tensors as T
 from _golden import frac, rows
 
-CASES = [("D3Q39", 3), ("D3Q103", 4), ("D3Q103", 3)]
+CASES = [("D3Q39", 3), ("D3Q103", 4), ("D3Q103", 3), ("D3Q729", 5), ("D3Q729", 4)]
 
 
 @pytest.fixture(scope="module")
 def lats():
-    return {n: L.by_name(n) for n in ("D3Q39", "D3Q103")}
+    return {n: L.by_name(n) for n in ("D3Q39", "D3Q103", "D3Q729")}
 
 
 def _random_state(lat, N, ncell=7, seed=1, eps=0.05):
@@ -119,6 +119,19 @@ def test_equal_times_reduce_to_regularised_bgk(lats, name, N):
     np.testing.assert_allclose(S.collide(f, model), want, atol=1e-13)
 
 
+def _harmonic_part(X):
+    """Traceless part of a symmetric tensor found by a linear solve rather than Appendix A's
+    closed form: H = X - sym(delta Y) with Y chosen so that tr H = 0 (least squares over every
+    rank r-2 tensor Y; the solution is exact because the trace map is onto)."""
+    r = X.ndim
+    basis = np.eye(3 ** (r - 2))
+    cols = [T.trace(T.sprod(np.eye(3), b.reshape((3,) * (r - 2)))).ravel() for b in basis]
+    y, *_ = np.linalg.lstsq(np.stack(cols, axis=1), T.trace(X).ravel(), rcond=None)
+    H = X - T.sprod(np.eye(3), y.reshape((3,) * (r - 2)))
+    assert np.abs(T.trace(H)).max() < 1e-12
+    return H
+
+
 def _pure_mode(n, m, rng):
     """A random pure irreducible mode A delta^m of order n, built from Appendix A's formulas."""
     d = np.eye(3)
@@ -137,13 +150,15 @@ def _pure_mode(n, m, rng):
             core = (X - 6 / 7 * T.sprod(d, T.trace(X))
                     + 3 / 35 * T.sprod(T.delta_power(2), T.trace_pow(X, 2)))
         else:
-            raise ValueError(r)
+            core = _harmonic_part(X)
     return T.sprod(core, T.delta_power(m)) if m else core
 
 
 @pytest.mark.parametrize("name,N,n,m", [("D3Q39", 3, 2, 0), ("D3Q39", 3, 3, 0), ("D3Q39", 3, 3, 1),
                                          ("D3Q103", 4, 2, 0), ("D3Q103", 4, 3, 0), ("D3Q103", 4, 3, 1),
-                                         ("D3Q103", 4, 4, 0), ("D3Q103", 4, 4, 1), ("D3Q103", 4, 4, 2)])
+                                         ("D3Q103", 4, 4, 0), ("D3Q103", 4, 4, 1), ("D3Q103", 4, 4, 2),
+                                         ("D3Q729", 5, 4, 1), ("D3Q729", 5, 5, 0), ("D3Q729", 5, 5, 1),
+                                         ("D3Q729", 5, 5, 2)])
 def test_single_mode_decays_at_its_own_rate(lats, name, N, n, m):
     """Eq. SMRT: a pure (n, m) mode on a moving, non-unit-temperature state is multiplied by
     exactly 1 - 1/tau_nm per collision, all other coefficients untouched (Galilean invariant)."""
