@@ -100,7 +100,9 @@ typedef struct {
  *   D3Q39 (N = 3), D3Q103 (N = 3, 4): every geometry and precision;
  *   D3Q729, the tensor product of D1Q9-P1 (Sec. 4.2, Table 3: d = 9, degree 11), N = 4, 5:
  *     batched 1D lines (ny = nz = 1), frame shift along x only, LB_F64 or LB_F32; weights
- *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint.
+ *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint. The states
+ *     passed to the stepping calls must start on 16-byte boundaries (LB_ERR_INVALID
+ *     otherwise): the kernel stages population segments with the bulk-copy engine.
  * hermite_order N: truncation order of Eqs. an/fi.
  * cuda_stream: cudaStream_t used for every later call on this context.
  * On success *out is a new context (relaxation times unset: lb_set_relaxation must follow).
@@ -147,7 +149,8 @@ lb_status lb_fill_equilibrium(lb_ctx *ctx, void *f, const double *rho, const dou
  * Errors: LB_ERR_INVALID (null, nsteps < 1, relaxation unset), LB_ERR_CUDA. */
 lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 
-/* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128);
+/* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128;
+ * on D3Q729 each warp of the block takes its own 32-cell tile);
  * persistent = 1: lb_step runs all its steps in one cooperative launch of blocks_per_sm
  * blocks per SM (0 = as many as fit), tiles spread over the blocks, a grid-wide barrier between
  * steps (its wait is bounded: on timeout the health word gets LB_HEALTH_TIMEOUT and the

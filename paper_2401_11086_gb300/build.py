@@ -64,6 +64,8 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     jobs = jobs or min(len(sources), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), sources))
+    for stale in set(glob.glob(os.path.join(BUILD, "*.o"))) - set(objs):  # objects of older sources
+        os.remove(stale)
     stamp = hashlib.sha256("".join(objs).encode()).hexdigest()[:16]
     stamp_file = os.path.join(BUILD, "libsmrt.stamp")
     if os.path.exists(LIB) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:

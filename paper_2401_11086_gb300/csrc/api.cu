@@ -263,9 +263,12 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         in.kx = k0;
         ncells += line ? (size_t)in.nx : (size_t)grid->nx * grid->ny * grid->nz;
     }
-    if (line) tiles = make_tiles(c->nx_inst, kTile);
+    // tensor-product contexts keep 32-cell tiles (one per warp); their tile width is the block
+    // size, 64 by default
+    const int width0 = tensor ? 64 : kTile;
+    if (line) tiles = make_tiles(c->nx_inst, tensor ? 32 : width0);
     c->max_tiles = line ? (long long)make_tiles(c->nx_inst, 32).size() : 0;
-    c->sched.tile_width = kTile;
+    c->sched.tile_width = line ? width0 : kTile;
     c->sched.blocks_per_sm = 0;
     c->sched.persistent = 0;
     c->sched.ms_per_step = 0.0;
@@ -294,7 +297,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     v.fixedx = grid->bc_x;
     v.ntiles = (int)tiles.size();
     v.ncells = (long long)ncells;
-    v.tile_width = kTile;
+    v.tile_width = line ? width0 : kTile;
 
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&c->d_inst, sizeof(InstanceInfo) * grid->batch);
@@ -424,6 +427,10 @@ lb_status check_pair(const lb_ctx *c, const void *fa, const void *fb, int nsteps
     const size_t bytes = c->elem * lb_state_elems(c);
     const char *a0 = static_cast<const char *>(fa), *b0 = static_cast<const char *>(fb);
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;  // overlap
+    // the tensor-product kernels copy population segments with the bulk-copy engine, which
+    // needs 16-byte aligned addresses
+    if (c->kind == 2 && ((reinterpret_cast<uintptr_t>(fa) | reinterpret_cast<uintptr_t>(fb)) & 15u))
+        return LB_ERR_INVALID;
     return LB_OK;
 }
 
@@ -433,7 +440,10 @@ long long persistent_grid(const lb_ctx *c) {
     const int occ = c->ks->occupancy(c->view);
     if (occ < 1) return 0;
     const int bps = c->sched.blocks_per_sm > 0 ? std::min(c->sched.blocks_per_sm, occ) : occ;
-    return std::max(1LL, std::min((long long)bps * c->num_sms, (long long)c->view.ntiles));
+    // blocks with work: one per tile, or per tile_width / 32 tiles on tensor-product sets
+    const long long wpb = c->kind == 2 ? c->view.tile_width / 32 : 1;
+    const long long needed = (c->view.ntiles + wpb - 1) / wpb;
+    return std::max(1LL, std::min((long long)bps * c->num_sms, needed));
 }
 
 cudaError_t launch_persistent(lb_ctx *c, const CtxView &v, void *fa, void *fb, int nsteps) {
@@ -469,7 +479,9 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
         c->sched = *s;
         return LB_OK;
     }
-    if (s->tile_width != c->view.tile_width) {
+    if (s->tile_width != c->view.tile_width && c->kind == 2) {
+        c->view.tile_width = s->tile_width;  // block size only: the tiles stay 32 cells wide
+    } else if (s->tile_width != c->view.tile_width) {
         const std::vector<int2> tiles = make_tiles(c->nx_inst, s->tile_width);
         if ((long long)tiles.size() > c->max_tiles) return LB_ERR_INVALID;
         cudaError_t e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(),

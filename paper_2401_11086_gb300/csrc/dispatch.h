@@ -208,27 +208,49 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
     return a;
 }
 
+// The warp-staged kernels may take more than the default 48 KB of dynamic shared memory:
+// raise the limit of each instantiation to what a 128-thread block needs (once per process).
+template <auto Kernel, class L1, class T>
+cudaError_t tp_smem_limit() {
+    static const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      int(TPWarpStage<L1, T>::bytes(128)));
+    return e;
+}
+
+// Tensor-product contexts keep 32-cell tiles; the schedule's tile width is the block size
+// (tile_width / 32 warps, one tile each).
+inline int tp_blocks(const CtxView &v) {
+    const int wpb = v.tile_width / 32;
+    return (v.ntiles + wpb - 1) / wpb;
+}
+
 template <class L1, int N, class T>
 cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
     const TPArgs<T> a = make_tp_args<T>(v, fin, fout);
-    if (v.fixedx)
-        tp_step_line_kernel<L1, N, T, true><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
-    else
-        tp_step_line_kernel<L1, N, T, false><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
+    const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
+    if (v.fixedx) {
+        const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true>, L1, T>();
+        if (e != cudaSuccess) return e;
+        tp_step_line_warp<L1, N, T, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles);
+    } else {
+        const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, false>, L1, T>();
+        if (e != cudaSuccess) return e;
+        tp_step_line_warp<L1, N, T, false><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles);
+    }
     return cudaGetLastError();
 }
 
 template <class L1, int N, class T>
 cudaError_t tp_launch_moments(const CtxView &v, const void *f, double *out, unsigned mask) {
     const TPArgs<T> a = make_tp_args<T>(v, f, nullptr);
-    tp_moments_kernel<L1, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(a, out, v.ncells, mask, v.fixedx);
+    tp_moments_kernel<L1, N, T><<<v.ntiles, 32, 0, v.stream>>>(a, out, v.ncells, mask, v.fixedx);
     return cudaGetLastError();
 }
 
 template <class L1, int N, class T>
 cudaError_t tp_launch_fill(const CtxView &v, void *f, const double *rho, const double *u, const double *theta) {
     const TPArgs<T> a = make_tp_args<T>(v, nullptr, f);
-    tp_fill_kernel<L1, N, T><<<v.ntiles, v.tile_width, 0, v.stream>>>(a, rho, u, theta, v.ncells);
+    tp_fill_kernel<L1, N, T><<<v.ntiles, 32, 0, v.stream>>>(a, rho, u, theta, v.ncells);
     return cudaGetLastError();
 }
 
@@ -246,7 +268,7 @@ cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nstep
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(v.tile_width);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = TPWarpStage<L1, T>::bytes(v.tile_width);
     cfg.stream = v.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -255,17 +277,32 @@ cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nstep
     cfg.numAttrs = 1;
     const int ntiles = v.ntiles;
     unsigned *bar = v.bar;
-    if (v.fixedx)
-        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent<L1, N, T, true>, a, nsteps, ntiles, bar);
-    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent<L1, N, T, false>, a, nsteps, ntiles, bar);
+    if (v.fixedx) {
+        const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true>, a, nsteps, ntiles, bar);
+    }
+    const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, false>, L1, T>();
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, false>, a, nsteps, ntiles, bar);
 }
 
 template <class L1, int N, class T>
 int tp_persistent_occupancy(const CtxView &v) {
     int n = 0;
-    const cudaError_t e =
-        v.fixedx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent<L1, N, T, true>, v.tile_width, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent<L1, N, T, false>, v.tile_width, 0);
+    const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
+    cudaError_t e;
+    if (v.fixedx) {
+        e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, true>,
+                                                              v.tile_width, smem);
+    } else {
+        e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, false>, L1, T>();
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, false>,
+                                                              v.tile_width, smem);
+    }
     return e == cudaSuccess ? n : 0;
 }
 

@@ -171,6 +171,111 @@ struct TPCell {
         }
     }
 
+    // Pieces of the same sums for a pipeline that sees one +-e_b pair of x-rows at a time.
+    // g_j = sum_a f_a e_a^j over one x-row; row(ic<a>) returns the population with x-index a.
+    template <class Row>
+    SMRT_D static void xrow(const Row &row, T (&g)[N + 1]) {
+        const T f0 = row(ic<0>{});
+        T S[NP1], D[NP1];
+        static_for<NP1>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            const T fp = row(ic<2 * p + 1>{});
+            const T fm = row(ic<2 * p + 2>{});
+            S[p] = fp + fm;
+            D[p] = fp - fm;
+        });
+        static_for<N + 1>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            T acc = (j == 0) ? f0 : T(0);
+            static_for<NP1>([&](auto P) {
+                constexpr int p = decltype(P)::value;
+                constexpr double ej = double(ipow(L1::E(p), j));
+                if constexpr (j == 0)
+                    acc = acc + S[p];
+                else if constexpr (j & 1)
+                    acc = fma(T(ej), D[p], acc);
+                else
+                    acc = fma(T(ej), S[p], acc);
+            });
+            g[j] = acc;
+        });
+    }
+    // h_(j,k) += sum_b g_(b)j e_b^k for the rest row (e_b = 0) ...
+    SMRT_D static void yrest(const T (&g)[N + 1], T (&h)[N + 1][N + 1]) {
+        static_for<N + 1>([&](auto J) { h[decltype(J)::value][0] += g[decltype(J)::value]; });
+    }
+    // ... and for the rows +e_b (gp) and -e_b (gm)
+    SMRT_D static void ypair(const T (&gp)[N + 1], const T (&gm)[N + 1], T eb, T (&h)[N + 1][N + 1]) {
+        T pw[N + 1];
+        pw[0] = T(1);
+        static_for<N>([&](auto K) { pw[decltype(K)::value + 1] = pw[decltype(K)::value] * eb; });
+        static_for<N + 1>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            const T s = gp[j] + gm[j], d = gp[j] - gm[j];
+            h[j][0] += s;
+            static_for<N - j>([&](auto K) {
+                constexpr int k = decltype(K)::value + 1;
+                h[j][k] = fma(pw[k], (k & 1) ? d : s, h[j][k]);
+            });
+        });
+    }
+    // R_(j,k,l) += e_c^l h_(j,k) at the end of z-plane c; h is cleared for the next one
+    SMRT_D static void zfold(T (&h)[N + 1][N + 1], T ec, T (&R)[M]) {
+        T pw[N + 1];
+        pw[0] = T(1);
+        static_for<N>([&](auto L) { pw[decltype(L)::value + 1] = pw[decltype(L)::value] * ec; });
+        static_for<M>([&](auto G) {
+            constexpr int g = decltype(G)::value;
+            constexpr int j = mi_comp(g, 0), k = mi_comp(g, 1), l = mi_comp(g, 2);
+            if constexpr (l == 0)
+                R[g] += h[j][k];
+            else
+                R[g] = fma(pw[l], h[j][k], R[g]);
+        });
+        static_for<N + 1>([&](auto J) {
+            static_for<N + 1 - decltype(J)::value>([&](auto K) { h[decltype(J)::value][decltype(K)::value] = T(0); });
+        });
+    }
+    // Rebuild side: Pc_(j,k) = sum_l P_(j,k,l) e_c^l for z-plane c ...
+    template <class U>
+    SMRT_D static void zplane(const U (&P)[M], U ec, U (&Pc)[N + 1][N + 1]) {
+        U pw[N + 1];
+        pw[0] = U(1);
+        static_for<N>([&](auto L) { pw[decltype(L)::value + 1] = pw[decltype(L)::value] * ec; });
+        static_for<N + 1>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            static_for<N + 1 - j>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                U acc = P[mi_pos(j, k, 0)];
+                static_for<N - j - k>([&](auto L) {
+                    constexpr int l = decltype(L)::value + 1;
+                    acc = fma(pw[l], P[mi_pos(j, k, l)], acc);
+                });
+                Pc[j][k] = acc;
+            });
+        });
+    }
+    // ... and the x-row coefficients Pb_j = sum_k Pc_(j,k) (+-e_b)^k of the rows +e_b, -e_b
+    template <class U>
+    SMRT_D static void yrows(const U (&Pc)[N + 1][N + 1], U eb, U (&Pp)[N + 1], U (&Pm)[N + 1]) {
+        U pw[N + 1];
+        pw[0] = U(1);
+        static_for<N>([&](auto K) { pw[decltype(K)::value + 1] = pw[decltype(K)::value] * eb; });
+        static_for<N + 1>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            U ev = Pc[j][0], od = U(0);
+            static_for<N - j>([&](auto K) {
+                constexpr int k = decltype(K)::value + 1;
+                if constexpr (k & 1)
+                    od = fma(pw[k], Pc[j][k], od);
+                else
+                    ev = fma(pw[k], Pc[j][k], ev);
+            });
+            Pp[j] = ev + od;
+            Pm[j] = ev - od;
+        });
+    }
+
     // a2, a4-a6 on the raw moments: R (in) -> rebuild coefficients P (out, same slots) with
     // f'_i = w_i sum_gamma P_gamma e_i^gamma. Returns false when rho or theta is not positive.
     SMRT_D static bool collide_moments(T (&R)[M], T c, const T *tauA, const T *tauB) {
@@ -351,76 +456,296 @@ struct TPCell {
     }
 };
 
-// ------------------------------------------------------------------------------ kernels
-// One thread per cell of tile tile_index (instance j, cells x0 .. x0 + blockDim - 1).
+// ------------------------------------------------------------------ async copies (sm_90+)
+SMRT_D unsigned smem_addr(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+SMRT_D void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+SMRT_D void mbar_arrive_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+// One contiguous global -> shared copy by the bulk-copy engine; its bytes count against the
+// transaction count of mbarrier b. Addresses and size must be multiples of 16 bytes.
+SMRT_D void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(b))
+                 : "memory");
+}
+// Order this thread's earlier generic-proxy accesses of shared (global) memory before its
+// later async-proxy ones: a buffer read or written by the threads, then refilled by the copy
+// engine; data written by other blocks, then copied.
+SMRT_D void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+SMRT_D void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Make mbarrier initialisations visible to the async proxy (the copy engine).
+SMRT_D void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+SMRT_D unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait until the phase of parity `parity` of mbarrier b has completed. Gives up after about a
+// second (or 2^26 polls) and returns false.
+SMRT_D bool mbar_wait(unsigned long long *b, unsigned parity) {
+    const unsigned addr = smem_addr(b);
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 0; spin < (1u << 26); ++spin) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 63u) == 63u && global_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ warp-staged line tile
+// Each warp owns a tile of 32 cells and its own copy pipeline, so no block-wide barrier is
+// ever taken inside a step. The step's d^3 pulls per cell reach shared memory by stage: stage
+// st covers z-plane c = st / (NP1 + 1) and, within it, either the rest x-row (e_b = 0, d
+// planes) or the pair of x-rows +e_b, -e_b (2 d planes). Each plane arrives as one contiguous
+// x-segment [x0 - k - E_max, x0 + 31 - k + E_max] (every pull of the tile, rounded out to 16
+// bytes), copied by the bulk-copy engine; kStages fills are in flight per warp, each counted
+// in bytes on its own mbarrier.
+template <class L1, class T>
+struct TPWarpStage {
+    static constexpr int kW = 32;                       // cells per warp tile
+    static constexpr int kStages = 3;                   // fills in flight per warp
+    static constexpr int kAlign = 16 / int(sizeof(T));  // elements per 16 bytes
+    static constexpr int kEmax = L1::E(L1::NP1 - 1);    // largest |e| of the 1D rule
+    static constexpr int kSeg = kW + ((2 * kEmax + kAlign - 1) + kAlign - 1) / kAlign * kAlign;
+    static constexpr int kRows = 2 * L1::Q1;            // planes of the largest stage
+    static constexpr int kPerZ = L1::NP1 + 1;           // stages per z-plane
+    static constexpr int kTotal = L1::Q1 * kPerZ;       // stages per step
+    static constexpr size_t kWarpBytes =                // mbarriers, then the stage buffers
+        (128 + size_t(kStages) * kRows * kSeg * sizeof(T) + 127) / 128 * 128;
+    SMRT_HD static size_t bytes(int threads) { return size_t(threads / 32) * kWarpBytes; }
+};
+
+// One warp tile of the step. buf, bar: the warp's stage buffers and mbarriers; bit b of parity
+// is the parity of buffer b's next fill, bit b of pending says that fill is in flight. All 32
+// lanes call it (lanes past the line's end idle). Returns false, with LB_HEALTH_TIMEOUT in
+// the health word, when a fill did not land within the bounded wait.
 template <class L1, int N, class T, bool FixedX, bool Coherent>
-SMRT_D void tp_line_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *__restrict__ fin,
-                         T *__restrict__ fout, int tile_index) {
+SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *__restrict__ fin,
+                         T *__restrict__ fout, int tile_index, T *buf, unsigned long long *bar, unsigned &parity,
+                         unsigned &pending) {
     using C = TPCell<L1, N, T>;
+    using S = TPWarpStage<L1, T>;
     constexpr int Q1 = L1::Q1;
-    constexpr int Q = Q1 * Q1 * Q1;
+    constexpr int NP1 = L1::NP1;
+    constexpr int P2 = Q1 * Q1;
+    constexpr int Q = P2 * Q1;
+    constexpr int EM = S::kEmax;
+    constexpr int SEG = S::kSeg;
+    constexpr int NS = S::kStages;
+    const int lane = threadIdx.x & 31;
     const int2 tile = a.tiles[tile_index];
     const InstanceInfo &in = a.inst[tile.x];
-    const int x = tile.y + threadIdx.x;
-    const int L = in.nx;
-    if (x >= L) return;
+    const int x0 = tile.y, x = x0 + lane, L = in.nx, kx = in.kx;
+    const bool active = x < L;
     const long long base = in.cell_off;
     const T *gl = a.ghosts + (long long)tile.x * 2 * Q;
     const T *gr = gl + Q;
-    // a1: the x-velocity e_a of a population fixes where it is pulled from: x - e_a - k
-    // (periodic lines wrap once: the reach plus |k| never exceeds the length)
-    int xs[Q1];
-    static_for<Q1>([&](auto A) {
-        constexpr int av = decltype(A)::value;
-        const int t = x - (e1<L1>(av) + in.kx);
-        xs[av] = FixedX ? t : wrap(t, L);
-    });
-    auto pop = [&](int i, auto A) -> T {
-        const int t = xs[decltype(A)::value];
-        if constexpr (FixedX) {
-            if (t < 0) return gl[i];
-            if (t >= L) return gr[i];
-        }
-        return load_pop<Coherent>(fin + (long long)s.plane[i] * a.stride + base + t);
+    // every plane contributes elements [g_al, g_al + SEG) of itself, clipped to [0, stride)
+    const long long g_al = (base + x0 - kx - EM) & ~(long long)(S::kAlign - 1);
+    const long long cs = g_al < 0 ? 0 : g_al;
+    const long long ce = (g_al + SEG < a.stride) ? g_al + SEG : a.stride;
+    const unsigned nbytes = unsigned((ce - cs) * (long long)sizeof(T));
+    const int dst_off = int(cs - g_al);
+    auto issue = [&](int st) {
+        const int sb = st % NS;
+        pending |= 1u << sb;
+        const int cz = st / S::kPerZ, p = st % S::kPerZ;
+        const int nplanes = p ? 2 * Q1 : Q1;
+        const int k0 = p ? (2 * p - 1) * Q1 : 0;  // in-plane index of the stage's first population
+        unsigned long long *b = bar + sb;
+        if constexpr (Coherent) fence_async_global();
+        fence_async_shared();
+        if (lane == 0) mbar_arrive_expect_tx(b, unsigned(nplanes) * nbytes);
+        if (lane < nplanes)
+            bulk_copy_g2s(buf + size_t(sb) * S::kRows * SEG + size_t(lane) * SEG + dst_off,
+                          fin + (long long)s.plane[cz * P2 + k0 + lane] * a.stride + cs, nbytes, b);
     };
+    // the lane's pull by x-velocity a of a staged row sits at row + a SEG + tb - e_a; each
+    // (plane, slot) is read by this lane only, so the lane may overwrite its own slots
+    const int tb = int(base + x - kx - g_al);
+    // pulls from beyond the line's ends: their slots get what the pull must see (the end
+    // state's population, or the wrapped population of a periodic line) once the fill lands
+    unsigned beyond = 0u;
+    if (active)
+        static_for<Q1>([&](auto A) {
+            constexpr int av = decltype(A)::value;
+            const int t = x - e1<L1>(av) - kx;
+            if (t < 0 || t >= L) beyond |= 1u << av;
+        });
+    for (int st = 0; st < NS; ++st) issue(st);
     T R[C::M];
-    C::project(pop, s.e, R);
-    const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in));
-    if (!ok) atomicOr(a.health, 1u);
-    T *dst = fout + base + x;
-    C::template rebuild<T>(R, s.e, s.w, [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; });
+    static_for<C::M>([&](auto G) { R[decltype(G)::value] = T(0); });
+    T h[N + 1][N + 1];
+    static_for<N + 1>([&](auto J) {
+        static_for<N + 1 - decltype(J)::value>([&](auto K) { h[decltype(J)::value][decltype(K)::value] = T(0); });
+    });
+#pragma unroll 1
+    for (int st = 0; st < S::kTotal; ++st) {
+        const int sb = st % NS;
+        const bool landed = __all_sync(0xffffffffu, mbar_wait(bar + sb, (parity >> sb) & 1u));
+        if (!landed) {
+            if (lane == 0) atomicOr(a.health, 2u);
+            // let fills still in flight land before the warp moves on (each wait bounded)
+            for (int q = 0; q < NS; ++q)
+                if ((pending >> q) & 1u) mbar_wait(bar + q, (parity >> q) & 1u);
+            return false;
+        }
+        parity ^= 1u << sb;
+        pending &= ~(1u << sb);
+        const int cz = st / S::kPerZ, p = st % S::kPerZ;
+        T *bs = buf + size_t(sb) * S::kRows * SEG;
+        if (active) {
+            if (beyond) {
+                const int nrows = p ? 2 : 1;
+                const int k0 = p ? (2 * p - 1) * Q1 : 0;
+                static_for<Q1>([&](auto A) {
+                    constexpr int av = decltype(A)::value;
+                    if ((beyond >> av) & 1u) {
+                        const int t = x - e1<L1>(av) - kx;
+                        for (int r = 0; r < nrows; ++r) {
+                            const int i = cz * P2 + k0 + r * Q1 + av;
+                            T v;
+                            if constexpr (FixedX)
+                                v = t < 0 ? gl[i] : gr[i];
+                            else
+                                v = load_pop<Coherent>(fin + (long long)s.plane[i] * a.stride + base + wrap(t, L));
+                            bs[(r * Q1 + av) * SEG + tb - e1<L1>(av)] = v;
+                        }
+                    }
+                });
+                fence_async_shared();  // own slots rewritten: before the buffer's next fill
+            }
+            const T *r0 = bs + tb;
+            auto rowp = [&](auto A) -> T {
+                constexpr int av = decltype(A)::value;
+                return r0[av * SEG - e1<L1>(av)];
+            };
+            if (p == 0) {
+                T g[N + 1];
+                C::xrow(rowp, g);
+                C::yrest(g, h);
+            } else {
+                const T *r1 = r0 + Q1 * SEG;
+                auto rowm = [&](auto A) -> T {
+                    constexpr int av = decltype(A)::value;
+                    return r1[av * SEG - e1<L1>(av)];
+                };
+                T gp[N + 1], gm[N + 1];
+                C::xrow(rowp, gp);
+                C::xrow(rowm, gm);
+                C::ypair(gp, gm, s.e[2 * p - 1], h);
+            }
+            if (p == NP1) C::zfold(h, s.e[cz], R);
+        }
+        __syncwarp();  // every lane is done with buffer sb
+        if (st + NS < S::kTotal) issue(st + NS);
+    }
+    if (active) {
+        const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in));
+        if (!ok) atomicOr(a.health, 1u);
+        T *dst = fout + base + x;
+        auto put = [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; };
+#pragma unroll 1
+        for (int cz = 0; cz < Q1; ++cz) {
+            T Pc[N + 1][N + 1];
+            C::template zplane<T>(R, s.e[cz], Pc);
+            const T wc = s.w[cz];
+            {
+                T Pb[N + 1];
+                static_for<N + 1>([&](auto J) { Pb[decltype(J)::value] = Pc[decltype(J)::value][0]; });
+                C::template emit_x<T>(Pb, wc * s.w[0], s.w, cz * P2, put);
+            }
+#pragma unroll 1
+            for (int p = 1; p <= NP1; ++p) {
+                T Pp[N + 1], Pm[N + 1];
+                C::template yrows<T>(Pc, s.e[2 * p - 1], Pp, Pm);
+                const T wbc = wc * s.w[2 * p - 1];
+                C::template emit_x<T>(Pp, wbc, s.w, cz * P2 + (2 * p - 1) * Q1, put);
+                C::template emit_x<T>(Pm, wbc, s.w, cz * P2 + 2 * p * Q1, put);
+            }
+        }
+    }
+    return true;
 }
 
-template <class L1, int N, class T, bool FixedX>
-__global__ void __launch_bounds__(128) tp_step_line_kernel(TPArgs<T> a) {
-    __shared__ TPTables<L1, T> s;
-    tp_load_tables<L1>(a, s);
-    tp_line_tile<L1, N, T, FixedX, false>(a, s, a.fin, a.fout, blockIdx.x);
+template <class L1, class T>
+SMRT_D void tp_warp_setup(unsigned char *dyn, unsigned long long *&bar, T *&buf) {
+    using S = TPWarpStage<L1, T>;
+    unsigned char *mine = dyn + size_t(threadIdx.x >> 5) * S::kWarpBytes;
+    bar = reinterpret_cast<unsigned long long *>(mine);
+    buf = reinterpret_cast<T *>(mine + 128);
+    if ((threadIdx.x & 31) == 0) {
+        for (int q = 0; q < S::kStages; ++q) mbar_init(bar + q, 1);
+        fence_mbar_init();
+    }
 }
 
-// All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh).
+// One step: warp w of block b takes the 32-cell tile b * (blockDim / 32) + w.
 template <class L1, int N, class T, bool FixedX>
-__global__ void __launch_bounds__(128) tp_step_line_persistent(TPArgs<T> a, int nsteps, int ntiles, unsigned *bar) {
+__global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles) {
     __shared__ TPTables<L1, T> s;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    unsigned long long *bar;
+    T *buf;
+    tp_warp_setup<L1>(dyn, bar, buf);
+    tp_load_tables<L1>(a, s);  // ends with __syncthreads
+    const int t = blockIdx.x * int(blockDim.x >> 5) + int(threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    unsigned parity = 0u, pending = 0u;
+    tp_warp_tile<L1, N, T, FixedX, false>(a, s, a.fin, a.fout, t, buf, bar, parity, pending);
+}
+
+// All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh); the
+// warps stride over the 32-cell tiles.
+template <class L1, int N, class T, bool FixedX>
+__global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a, int nsteps, int ntiles,
+                                                                    unsigned *barg) {
+    __shared__ TPTables<L1, T> s;
+    __shared__ int failed;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    unsigned long long *bar;
+    T *buf;
+    tp_warp_setup<L1>(dyn, bar, buf);
+    if (threadIdx.x == 0) failed = 0;
     tp_load_tables<L1>(a, s);
+    const int wpb = int(blockDim.x >> 5);
+    unsigned parity = 0u, pending = 0u;
     unsigned gen = 0;
-    if (threadIdx.x == 0) gen = atomicAdd(&bar[1], 0u);
-    const unsigned step0 = __ldcg(&bar[2]);
+    if (threadIdx.x == 0) gen = atomicAdd(&barg[1], 0u);
+    const unsigned step0 = __ldcg(&barg[2]);
     const T *src = a.fin;
     T *dst = a.fout;
     for (int st = 0; st < nsteps; ++st) {
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
-            tp_line_tile<L1, N, T, FixedX, true>(a, s, src, dst, t);
+        for (int t = blockIdx.x * wpb + int(threadIdx.x >> 5); t < ntiles; t += gridDim.x * wpb)
+            if (!tp_warp_tile<L1, N, T, FixedX, true>(a, s, src, dst, t, buf, bar, parity, pending)) {
+                failed = 1;
+                break;
+            }
+        __syncthreads();
+        if (failed) return;
         if (st + 1 < nsteps) {
-            if (!grid_barrier(bar, gen, a.health)) return;
+            if (!grid_barrier(barg, gen, a.health)) return;
             const T *nsrc = dst;
             dst = (dst == a.fout) ? const_cast<T *>(a.fin) : a.fout;
             src = nsrc;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) bar[2] = step0 + unsigned(nsteps);
+    if (blockIdx.x == 0 && threadIdx.x == 0) barg[2] = step0 + unsigned(nsteps);
 }
 
+// ------------------------------------------------------------------------------ kernels
 // lb_moments of the pulled (pre-collision) populations.
 template <class L1, int N, class T>
 __global__ void __launch_bounds__(128) tp_moments_kernel(TPArgs<T> a, double *out, long long ncells,
