@@ -316,6 +316,128 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+# double-precision operations per cell-step of the D3Q729, N = 5 step kernel (ncu: DFMA x 2 +
+# DADD + DMUL over one launch of the 512-shock workload, divided by its cells), and the
+# nominal FP64 rate of a GB300
+TP_FP64_FLOP_PER_CELL = 15301.0
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def table3_instances(rank: int, count: int = 512):
+    """The D3Q729 workload of one rank: count shocks cycling over Table 3's rows (Ma 1.5, 3, 5
+    with their theta1), lengths 100..400 cells drawn with seed 11086 + rank."""
+    import numpy as np
+    from paper_2401_11086_gb300 import shocks
+    machs = [(1.5, 3.0, 5.0)[j % 3] for j in range(count)]
+    lengths = np.random.default_rng(11086 + rank).integers(100, 401, count)
+    return machs, lengths, [shocks.TABLE3_THETA1[m] for m in machs]
+
+
+def oracle_table3_rate(steps: int) -> dict:
+    """FP64 oracle on one Table 3 shock (Ma = 3, 100 cells, D3Q729, N = 5), single-threaded."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import synthetic
+from oracle import lattice as L, shock as K, smrt as S
+lat = L.d3q729()
+case = K.shock_case(lat, 5, 3.0, 100, theta1=0.333)
+st = case.states
+h = K.initial_state(case, *[synthetic.step_blend(100, st[k + "1"], st[k + "2"]) for k in ("rho", "u", "theta")])
+h = S.step(h, case.model, case.geom)
+t0 = time.perf_counter()
+for _ in range({steps}):
+    h = S.step(h, case.model, case.geom)
+dt = time.perf_counter() - t0
+print(json.dumps({{"rate": 100 * 729 * {steps} / dt, "seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_table3(args, world: int, rank: int, local: int) -> None:
+    """The paper's configuration (Sec. 4.2, Table 3): D3Q729 = D1Q9-P1^3, N = 5, SMRT times of
+    Table 4, step initial condition, fixed end states; 512 shocks per GPU cycling over the
+    rows Ma = 1.5, 3, 5 (theta1 = 0.714, 0.333, 0.167, k_x = 2), 100..400 cells each."""
+    import torch
+
+    import paper_2401_11086_gb300 as P
+    from paper_2401_11086_gb300 import shocks
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    machs, lengths, theta1 = table3_instances(rank)
+    d = P.lb_lattice_named("D3Q729")
+    stream = torch.cuda.current_stream()
+    prec = args.precision
+    ctx, f0, _ = shocks.setup_batch(d, 5, machs, lengths, precision=prec, width=0.0, theta1=theta1,
+                                    stream=stream)
+    P.lb_set_schedule(ctx, 64, 0, 0)
+    fa, fb = f0, ctx.new_state()
+    cur = P.lb_step(ctx, fa, fb, args.warmup)
+    other = fb if cur is fa else fa
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(K):
+        ev[i][0].record(stream)
+        cur = P.lb_step(ctx, cur, other, 1)
+        ev[i][1].record(stream)
+        other = fa if cur is fb else fb
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    st, flags = P.lb_poll_status(ctx)
+    if st != 0:
+        raise SystemExit(f"health word reports status {st} (flags {flags})")
+    cells = int(sum(lengths))
+    q = 729
+    elem = 8 if prec == "f64" else 4
+    kern_ms = ms / K
+    rate, ms = job_rate(cells * q * K, ms, dist)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak()
+    alg_bytes = 2.0 * q * elem * cells
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)",
+            "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": kern_ms,
+            "note": "issue-bound: the HBM fraction says how far from the memory roofline"}
+    if prec == "f64":
+        # the FP64 pipe bounds the double kernel: its double-precision operations per
+        # cell-step (ncu instruction counts, an FMA counted as two) against the nominal rate
+        gflop = TP_FP64_FLOP_PER_CELL * cells / (kern_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": gflop, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)",
+                "frac": gflop / FP64_PEAK_GFLOPS, "traffic": None, "peak_kind": "nominal FP64 rate",
+                "flop_per_cell": TP_FP64_FLOP_PER_CELL, "kernel_ms": kern_ms,
+                "hbm_frac": achieved / peak}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_table3_rate(40)
+        cpu = {"value": r["rate"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one Table 3 shock (Ma = 3, 100 cells, D3Q729, N = 5), 40 FP64 oracle steps"}
+    line = {"metric": METRIC, "value": rate / 1e9, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"table3_d3q729_n5_{prec}", "instances_per_gpu": len(machs),
+                       "cells_per_gpu": cells, "velocities": q, "hermite_order": 5,
+                       "state_bytes": elem * int(ctx.state_elems),
+                       "l2": "inputs larger than L2" if q * elem * cells > 129e6 else
+                             "inputs smaller than L2 (steps timed one by one)"},
+            "roofline": roof, "cpu_baseline": cpu, "gpu_launches": K, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,8 +447,11 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "batched"],
-                    help="box: the 256^3 roofline case (default); batched: 64 1D shocks")
+    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3"],
+                    help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
+                         "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
+                    help="table3 workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -336,6 +461,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "ours" and args.workload == "batched":
         run_batched(args, world, rank, local)
+        return
+    if args.impl == "ours" and args.workload == "table3":
+        run_table3(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, rank)
