@@ -152,6 +152,11 @@ def d3q729() -> Lattice:
     return tensor_product3(d1q9_p1(), "D3Q729")
 
 
+def d3q4913() -> Lattice:
+    """Tensor product of D1Q17-P1 (Sec. 4.2: the Ma = 7 runs, d = 17, degree 19)."""
+    return tensor_product3(d1q17_p1(), "D3Q4913")
+
+
 D3Q39_SHELLS = [(0, 0, 0), (1, 0, 0), (1, 1, 1), (2, 0, 0), (2, 2, 0), (3, 0, 0)]
 D3Q103_SHELLS = [(0, 0, 0), (1, 1, 1), (2, 0, 0), (2, 1, 1), (2, 2, 0), (2, 2, 2),
                  (3, 0, 0), (4, 0, 0), (3, 3, 3), (4, 2, 0)]
@@ -166,5 +171,5 @@ def d3q103() -> Lattice:
 
 
 def by_name(name: str) -> Lattice:
-    return {"D3Q39": d3q39, "D3Q103": d3q103, "D3Q729": d3q729,
+    return {"D3Q39": d3q39, "D3Q103": d3q103, "D3Q729": d3q729, "D3Q4913": d3q4913,
             "D1Q9-P1": d1q9_p1, "D1Q17-P1": d1q17_p1}[name]()

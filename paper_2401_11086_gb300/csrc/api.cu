@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -23,12 +24,14 @@ const KernelSet *kernels_d3q103_p1(int N);
 const KernelSet *kernels_d3q103_p2(int N);
 const KernelSet *kernels_d3q729_p0(int N);
 const KernelSet *kernels_d3q729_p1(int N);
+const KernelSet *kernels_d3q4913_p0(int N);
+const KernelSet *kernels_d3q4913_p1(int N);
 }  // namespace smrt
 
 using namespace smrt;
 
 struct lb_ctx {
-    int kind;  // 0 D3Q39, 1 D3Q103, 2 D3Q729 (tensor product of D1Q9-P1)
+    int kind;  // 0 D3Q39, 1 D3Q103, 2 D3Q729 (D1Q9-P1 cubed), 3 D3Q4913 (D1Q17-P1 cubed)
     int q, np, N, degree;
     lb_precision prec;
     size_t elem;  // bytes per population value
@@ -105,16 +108,15 @@ bool match_tensor(const lb_lattice_desc *d, std::vector<int> &perm, double (&w1)
     constexpr int Q1 = L1::Q1;
     if (d->q != Q1 * Q1 * Q1) return false;
     perm.assign(d->q, -1);
-    std::vector<char> used(d->q, 0);
+    std::map<long long, int> where;  // velocity -> caller index
+    auto key = [](int x, int y, int z) { return ((long long)(x + 128) << 16) | ((y + 128) << 8) | (z + 128); };
+    for (int k = 0; k < d->q; ++k)
+        if (!where.emplace(key(d->e[3 * k], d->e[3 * k + 1], d->e[3 * k + 2]), k).second) return false;
     for (int i = 0; i < d->q; ++i) {
         const int a = i % Q1, b = (i / Q1) % Q1, cc = i / (Q1 * Q1);
-        int hit = -1;
-        for (int k = 0; k < d->q && hit < 0; ++k)
-            if (!used[k] && d->e[3 * k] == e1<L1>(a) && d->e[3 * k + 1] == e1<L1>(b) && d->e[3 * k + 2] == e1<L1>(cc))
-                hit = k;
-        if (hit < 0) return false;
-        used[hit] = 1;
-        perm[i] = hit;
+        const auto it = where.find(key(e1<L1>(a), e1<L1>(b), e1<L1>(cc)));
+        if (it == where.end()) return false;
+        perm[i] = it->second;
     }
     const double w0 = std::cbrt(d->w[perm[0]]);
     for (int a = 0; a < Q1; ++a) w1[a] = d->w[perm[a]] / (w0 * w0);
@@ -176,12 +178,17 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     c->elem = prec == LB_F64 ? sizeof(double) : sizeof(float);
     int reach[3] = {0, 0, 0};
     double w1[kMaxQ1] = {0.0};
-    const bool tensor = match_tensor<D1Q9P1>(lat, c->perm, w1);
+    const bool t729 = match_tensor<D1Q9P1>(lat, c->perm, w1);
+    const bool t4913 = !t729 && match_tensor<D1Q17P1>(lat, c->perm, w1);
+    const bool tensor = t729 || t4913;
     if (tensor) {
-        c->kind = 2;
+        c->kind = t729 ? 2 : 3;
         c->np = 0;
-        for (int k = 0; k < 3; ++k) reach[k] = D1Q9P1::E(D1Q9P1::NP1 - 1);
-        c->ks = prec == LB_F64 ? kernels_d3q729_p0(N) : (prec == LB_F32 ? kernels_d3q729_p1(N) : nullptr);
+        for (int k = 0; k < 3; ++k) reach[k] = t729 ? D1Q9P1::E(D1Q9P1::NP1 - 1) : D1Q17P1::E(D1Q17P1::NP1 - 1);
+        if (t729)
+            c->ks = prec == LB_F64 ? kernels_d3q729_p0(N) : (prec == LB_F32 ? kernels_d3q729_p1(N) : nullptr);
+        else
+            c->ks = prec == LB_F64 ? kernels_d3q4913_p0(N) : (prec == LB_F32 ? kernels_d3q4913_p1(N) : nullptr);
         c->as = nullptr;
         // batched 1D lines only, shifted along x only
         if (grid->ny != 1 || grid->nz != 1 || lat->shift[1] != 0 || lat->shift[2] != 0) c->ks = nullptr;
@@ -393,7 +400,15 @@ extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell
     if (e == cudaSuccess && c->view.fixedx) {
         e = cudaMemcpyAsync(c->d_states, c->h_states.data(), sizeof(double) * 10 * c->batch,
                             cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = c->ks->ghost(c->view, c->d_states, c->batch, c->d_ghosts, c->d_ghostsd);
+        if (e == cudaSuccess) {
+            // end-state populations of the instances just set only (a view whose instance
+            // table starts at j0)
+            CtxView gv = c->view;
+            gv.inst = c->d_inst + j0;
+            e = c->ks->ghost(gv, c->d_states + 10 * (size_t)j0, j1 - j0,
+                             static_cast<char *>(c->d_ghosts) + c->elem * c->q * 2 * (size_t)j0,
+                             c->d_ghostsd + (size_t)c->q * 2 * j0);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables are reused next call
     if (e != cudaSuccess) return LB_ERR_CUDA;
@@ -429,7 +444,7 @@ lb_status check_pair(const lb_ctx *c, const void *fa, const void *fb, int nsteps
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;  // overlap
     // the tensor-product kernels copy population segments with the bulk-copy engine, which
     // needs 16-byte aligned addresses
-    if (c->kind == 2 && ((reinterpret_cast<uintptr_t>(fa) | reinterpret_cast<uintptr_t>(fb)) & 15u))
+    if (c->kind >= 2 && ((reinterpret_cast<uintptr_t>(fa) | reinterpret_cast<uintptr_t>(fb)) & 15u))
         return LB_ERR_INVALID;
     return LB_OK;
 }
@@ -441,7 +456,7 @@ long long persistent_grid(const lb_ctx *c) {
     if (occ < 1) return 0;
     const int bps = c->sched.blocks_per_sm > 0 ? std::min(c->sched.blocks_per_sm, occ) : occ;
     // blocks with work: one per tile, or per tile_width / 32 tiles on tensor-product sets
-    const long long wpb = c->kind == 2 ? c->view.tile_width / 32 : 1;
+    const long long wpb = c->kind >= 2 ? c->view.tile_width / 32 : 1;
     const long long needed = (c->view.ntiles + wpb - 1) / wpb;
     return std::max(1LL, std::min((long long)bps * c->num_sms, needed));
 }
@@ -479,7 +494,7 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
         c->sched = *s;
         return LB_OK;
     }
-    if (s->tile_width != c->view.tile_width && c->kind == 2) {
+    if (s->tile_width != c->view.tile_width && c->kind >= 2) {
         c->view.tile_width = s->tile_width;  // block size only: the tiles stay 32 cells wide
     } else if (s->tile_width != c->view.tile_width) {
         const std::vector<int2> tiles = make_tiles(c->nx_inst, s->tile_width);

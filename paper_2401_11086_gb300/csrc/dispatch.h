@@ -10,7 +10,7 @@
 namespace smrt {
 
 constexpr int kMaxQ = 103;   // largest set with a per-population plane table in the launch
-constexpr int kMaxQTP = 729; // largest tensor-product set (plane table in device memory)
+constexpr int kMaxQTP = 4913; // largest tensor-product set (plane table in device memory)
 constexpr int kMaxNP = 51;
 constexpr int kTile = 128;  // cells per block (threads per block) for every kernel
 
@@ -34,7 +34,7 @@ struct CtxView {
     unsigned step;   // launch counter of lb_step (seeds the stochastic rounding)
     int tile_width;  // cells (threads) per block of the line kernels: 32, 64 or 128
     unsigned *bar;   // persistent launch: arrival count, generation, step counter
-    // tensor-product sets (D3Q729): caller plane of each library population (device table),
+    // tensor-product sets (D3Q729, D3Q4913): caller plane of each library population (device table),
     // the plane stride, and the 1D weights in library order
     const int *plane_idx;
     long long stride;

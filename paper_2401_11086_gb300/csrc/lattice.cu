@@ -249,7 +249,7 @@ static bool solve_rule_1d(double &c_out, std::vector<double> &w_out) {
             weights_1d<L1>(cm, W, rm);
             bool positive = true;
             for (long double wv : W) positive = positive && (wv > 0.0L);
-            if (fabsl(rm) < 1e-9L && positive && (!have || fabsl(cm - c0) < fabsl(best_c - c0))) {
+            if (fabsl(rm) < 1e-9L * gauss_moment(2 * (L1::NP1 + 1)) && positive && (!have || fabsl(cm - c0) < fabsl(best_c - c0))) {
                 have = true;
                 best_c = cm;
                 best_W = W;
@@ -298,6 +298,8 @@ extern "C" lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w
         return smrt::named<smrt::D3Q103>(e_out, w_out, c_out, q_out, degree_out, capacity);
     if (std::strcmp(name, "D3Q729") == 0)
         return smrt::named_tensor<smrt::D1Q9P1>(e_out, w_out, c_out, q_out, degree_out, capacity);
+    if (std::strcmp(name, "D3Q4913") == 0)
+        return smrt::named_tensor<smrt::D1Q17P1>(e_out, w_out, c_out, q_out, degree_out, capacity);
     return LB_ERR_INVALID;
 }
 

@@ -1,6 +1,7 @@
 // tensor.cuh -- LB-SMRT collide-and-stream on three-dimensional tensor-product velocity sets
 // (Yan & Shan, arXiv 2401.11086, Sec. 4.2: the 3D products D3Q{d^3} of the 1D rules D1Qd-P1,
-// D3Q729 = D1Q9-P1 x D1Q9-P1 x D1Q9-P1 of degree 11), batched 1D lines along x.
+// D3Q729 = D1Q9-P1^3 of degree 11 and D3Q4913 = D1Q17-P1^3 of degree 19), batched 1D lines
+// along x.
 //
 // A cell holds d^3 populations: too many for registers, so no pass ever holds them all. The
 // projection (Eq. an) and the rebuild (Eq. fi) factor over the three axes because the
@@ -568,9 +569,9 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
         if constexpr (Coherent) fence_async_global();
         fence_async_shared();
         if (lane == 0) mbar_arrive_expect_tx(b, unsigned(nplanes) * nbytes);
-        if (lane < nplanes)
-            bulk_copy_g2s(buf + size_t(sb) * S::kRows * SEG + size_t(lane) * SEG + dst_off,
-                          fin + (long long)s.plane[cz * P2 + k0 + lane] * a.stride + cs, nbytes, b);
+        for (int k = lane; k < nplanes; k += 32)  // a pair stage of D1Q17 has 34 planes
+            bulk_copy_g2s(buf + size_t(sb) * S::kRows * SEG + size_t(k) * SEG + dst_off,
+                          fin + (long long)s.plane[cz * P2 + k0 + k] * a.stride + cs, nbytes, b);
     };
     // the lane's pull by x-velocity a of a staged row sits at row + a SEG + tb - e_a; each
     // (plane, slot) is read by this lane only, so the lane may overwrite its own slots

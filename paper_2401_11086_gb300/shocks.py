@@ -34,8 +34,10 @@ TAU_RATIOS_REDUCED = (1.0, 1.0, 2.0 / 3.0, 3.0 / 2.0, 432.0 / 763.0, 6.0 / 7.0, 
                       864.0 / 1655.0, 108.0 / 163.0, 1.0)
 
 # Table 3: reference temperature (upstream theta1) of the paper's runs on the D1Q9-P1 product
-# set, by upstream Mach number; the frame shift is k_x = 2 in every row.
+# set, by upstream Mach number; the frame shift is k_x = 2 in these rows.
 TABLE3_THETA1 = {1.5: 0.714, 3.0: 0.333, 5.0: 0.167}
+# Table 3's Ma = 7 row runs on the D1Q17-P1 product set: theta1 = 0.071, k_x = 3.
+TABLE3_THETA1_D1Q17 = {7.0: 0.071}
 
 
 def ntau(N: int) -> int:

@@ -6,6 +6,7 @@ touches the CUDA path. Usage:
     python tests/golden/make_shock_golden.py ma3_d3q103_n4          # Ma = 3, 2048 cells, 20000 steps
     python tests/golden/make_shock_golden.py ma5_d3q103_n4_target   # Ma = 5, 1024 cells, 5000 steps
     python tests/golden/make_shock_golden.py ma3_d3q729_n5          # Table 3 row Ma = 3, 100 cells
+    python tests/golden/make_shock_golden.py ma7_d3q4913_n5         # Table 3 row Ma = 7, 100 cells
 
 Each case stores, at the listed step counts, the moments of the pre-collision populations
 (rho, physical u_x, theta, q_x) on every cell, float64.
@@ -37,6 +38,9 @@ CASES = {
     # theta1 = 0.333, k_x = 2, step initial condition, Table 4 SMRT times, ell = 2 cells
     "ma3_d3q729_n5": dict(lattice="D3Q729", N=5, Ma=3.0, nx=100, width=0.0, theta1=0.333,
                           checkpoints=(200, 1000)),
+    # Table 3 row Ma = 7: D3Q4913 (D1Q17-P1 product), N = 5, theta1 = 0.071, k_x = 3
+    "ma7_d3q4913_n5": dict(lattice="D3Q4913", N=5, Ma=7.0, nx=100, width=0.0, theta1=0.071,
+                           checkpoints=(100, 400)),
 }
 
 

@@ -43,7 +43,7 @@ def test_error_strings(lib):
     assert lib.lb_error_string(99) == b"unknown status"
 
 
-@pytest.mark.parametrize("name", ["D3Q39", "D3Q103", "D3Q729"])
+@pytest.mark.parametrize("name", ["D3Q39", "D3Q103", "D3Q729", "D3Q4913"])
 def test_library_lattice_agrees_with_oracle(lib, name):
     import paper_2401_11086_gb300 as P
     d = P.lb_lattice_named(name)
@@ -51,8 +51,11 @@ def test_library_lattice_agrees_with_oracle(lib, name):
     assert d.q == o.q and d.degree == o.degree
     assert abs(d.c - o.c) < 1e-13
     key = {tuple(e): w for e, w in zip(o.e.tolist(), o.w)}
+    # two independent solvers (least squares in double, bisection in long double); the
+    # degree-19 moment system behind D3Q4913 reaches moments of 17!! ~ 3e7; the two agree to 2e-12
+    tol = 5e-12 if name == "D3Q4913" else 1e-13
     for e, w in zip(d.e.tolist(), d.w):
-        assert abs(key[tuple(e)] - w) < 1e-13 * max(w, 1e-3)
+        assert abs(key[tuple(e)] - w) < tol * max(w, 1e-3)
 
 
 @pytest.mark.parametrize("Ma", [1.2, 1.5, 3.0, 5.0, 7.0])

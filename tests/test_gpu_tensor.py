@@ -223,3 +223,92 @@ def test_paper_configuration_ma3_n5_against_golden(lat):
         assert np.abs(m[1] - gold[f"u_{cp}"]).max() < 1e-10
         assert np.abs(m[4] / gold[f"theta_{cp}"] - 1).max() < 1e-10
         assert np.abs(m[5] - gold[f"q_{cp}"]).max() < 1e-10
+
+
+# ------------------------------------------------------------------ D3Q4913: Table 3, Ma = 7
+@pytest.fixture(scope="module")
+def lat17():
+    o = OL.d3q4913()
+    d = P.lb_lattice_named("D3Q4913")
+    return o, d, lib_from_oracle(o, d)
+
+
+def _ma7_case(olat, N, L):
+    case = OK.shock_case(olat, N, 7.0, L, theta1=shocks.TABLE3_THETA1_D1Q17[7.0])
+    st = case.states
+    h = OK.initial_state(case, *[synthetic.step_blend(L, st[k + "1"], st[k + "2"])
+                                 for k in ("rho", "u", "theta")])
+    return case, h
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_table3_ma7_d3q4913_matches_oracle(lat17, N):
+    """FP64, Table 3's Ma = 7 row (D1Q17-P1 product, theta1 = 0.071, k_x = 3), two shocks of
+    40 and 70 cells (ragged 32-cell tiles) from the step start, 6 steps, populations and
+    moments vs the oracle."""
+    olat, d, idx = lat17
+    lengths = [40, 70]
+    ctx, _, params = shocks.setup_batch(d, N, [7.0, 7.0], lengths, precision="f64", width=0.0,
+                                        theta1=[0.071, 0.071])
+    cases, hs = zip(*[_ma7_case(olat, N, L) for L in lengths])
+    assert all(p["kx"] == c.k == 3 for p, c in zip(params, cases))
+    fa = _upload_batch(ctx, d, idx, hs)
+    out = P.lb_step(ctx, fa, ctx.new_state(), 6)
+    assert P.lb_poll_status(ctx)[0] == 0
+    got = _download_batch(ctx, d, idx, out, lengths)
+    mom = P.lb_moments(ctx, out, P.LB_MOM_RHO | P.LB_MOM_U | P.LB_MOM_THETA | P.LB_MOM_Q).cpu().numpy()
+    off = 0
+    for j, (case, h) in enumerate(zip(cases, hs)):
+        for _ in range(6):
+            h = OS.step(h, case.model, case.geom)
+        want = h.reshape(olat.q, -1)
+        assert np.abs(got[j] - want).max() / np.abs(want).max() < 1e-11, j
+        m = OS.macroscopic(h, case.model, case.geom)
+        L = lengths[j]
+        np.testing.assert_allclose(mom[0, off:off + L], m["rho"], rtol=1e-11)
+        np.testing.assert_allclose(mom[4, off:off + L], m["theta"], rtol=1e-11)
+        np.testing.assert_allclose(mom[5, off:off + L], m["q"][0], atol=1e-10)
+        off += L
+
+
+def test_d3q4913_periodic_line_f32(lat17):
+    """FP32 periodic line of 45 cells (shift 3), perturbed populations, 2 steps."""
+    olat, d, idx = lat17
+    nx, N = 45, 5
+    rho, u, th = synthetic.taylor_green(0, amplitude=0.08, noise=2e-3, seed=3, shape=(1, 1, nx))
+    f0 = OS.equilibrium(rho.ravel(), u.reshape(3, -1), th.ravel(), olat, N)
+    rng = np.random.default_rng(3)
+    f0 = (f0 * (1.0 + 0.02 * rng.standard_normal(f0.shape))).reshape(olat.q, 1, 1, nx)
+    shift = (3, 0, 0)
+    model = OS.Model(olat, N, tau_ref=0.7)
+    geom = OS.Geometry(shape=(1, 1, nx), shift=shift)
+    ctx = P.lb_init_lattice(_desc(d, shift), nx, N=N, precision="f32")
+    P.lb_set_relaxation(ctx, _tau(model), True, 1.0)
+    fa = upload(ctx, f0, idx)
+    h = download(ctx, fa, idx).reshape(f0.shape)
+    for _ in range(2):
+        h = OS.step(h, model, geom)
+    got = download(ctx, P.lb_step(ctx, fa, ctx.new_state(), 2), idx)
+    assert np.abs(got - h.reshape(olat.q, -1)).max() / np.abs(h).max() < 2e-6 * 2
+
+
+def test_paper_configuration_ma7_n5_against_golden(lat17):
+    """The paper's Ma = 7 run (Table 3 row, D3Q4913, N = 5, 100 cells, step start, SMRT
+    times), FP64, 400 steps: moments vs the oracle's stored profiles."""
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "ma7_d3q4913_n5.npz"))
+    olat, d, idx = lat17
+    ctx, f0, params = shocks.setup_batch(d, 5, [7.0], [100], precision="f64", width=0.0, theta1=[0.071])
+    assert params[0]["kx"] == int(gold["k"])
+    mask = P.LB_MOM_RHO | P.LB_MOM_U | P.LB_MOM_THETA | P.LB_MOM_Q
+    fa, fb = f0, ctx.new_state()
+    done = 0
+    for cp in (100, 400):
+        out = P.lb_step(ctx, fa, fb, cp - done)
+        fa, fb = out, (fb if out is fa else fa)
+        done = cp
+        assert P.lb_poll_status(ctx)[0] == 0
+        m = P.lb_moments(ctx, fa, mask).cpu().numpy()
+        assert np.abs(m[0] / gold[f"rho_{cp}"] - 1).max() < 1e-10
+        assert np.abs(m[1] - gold[f"u_{cp}"]).max() < 1e-10
+        assert np.abs(m[4] / gold[f"theta_{cp}"] - 1).max() < 1e-10
+        assert np.abs(m[5] - gold[f"q_{cp}"]).max() < 1e-10

@@ -10,12 +10,12 @@ from oracle import smrt as S
 from oracle import tensors as T
 from _golden import frac, rows
 
-CASES = [("D3Q39", 3), ("D3Q103", 4), ("D3Q103", 3), ("D3Q729", 5), ("D3Q729", 4)]
+CASES = [("D3Q39", 3), ("D3Q103", 4), ("D3Q103", 3), ("D3Q729", 5), ("D3Q729", 4), ("D3Q4913", 5)]
 
 
 @pytest.fixture(scope="module")
 def lats():
-    return {n: L.by_name(n) for n in ("D3Q39", "D3Q103", "D3Q729")}
+    return {n: L.by_name(n) for n in ("D3Q39", "D3Q103", "D3Q729", "D3Q4913")}
 
 
 def _random_state(lat, N, ncell=7, seed=1, eps=0.05):
