@@ -98,7 +98,8 @@ typedef struct {
  * the exactness remark after Eq. fi); the library checks this by brute force and also
  * matches e against the velocity sets it has kernels for (LB_ERR_UNSUPPORTED otherwise):
  *   D3Q39 (N = 3), D3Q103 (N = 3, 4): every geometry and precision;
- *   D3Q729, the tensor product of D1Q9-P1 (Sec. 4.2, Table 3: d = 9, degree 11), N = 4, 5:
+ *   D3Q729 and D3Q4913, the tensor products of D1Q9-P1 and D1Q17-P1 (Sec. 4.2, Table 3:
+ *   d = 9, degree 11; d = 17, degree 19), N = 4, 5:
  *     batched 1D lines (ny = nz = 1), frame shift along x only, LB_F64 or LB_F32; weights
  *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint. The states
  *     passed to the stepping calls must start on 16-byte boundaries (LB_ERR_INVALID
@@ -258,7 +259,9 @@ int lb_num_moment_rows(const lb_ctx *ctx, unsigned which_mask);
  * conditions of a degree-Q Gauss-Hermite rule (Sec. 3, Eq. an): "D3Q39" (degree 7),
  * "D3Q103" (degree 9) and "D3Q729" (degree 11, the 3D tensor product of the 1D rule D1Q9-P1
  * on c {0, +-1, +-2, +-3, +-5} of Sec. 4.2 / Table 3, in the order i = a + 9 b + 81 c over the
- * 1D indices a, b, c = rest, +1, -1, +2, -2, +3, -3, +5, -5).
+ * 1D indices a, b, c = rest, +1, -1, +2, -2, +3, -3, +5, -5) and "D3Q4913" (degree 19, the
+ * product of D1Q17-P1 on c {0, +-1, .., +-7, +-9}, i = a + 17 b + 289 c, 1D order rest, +1, -1,
+ * .., +7, -7, +9, -9).
  * Writes up to capacity velocities: e_out (capacity*3 int8), w_out
  * (capacity doubles), *c_out, *q_out, *degree_out (host memory).
  * Errors: LB_ERR_INVALID (unknown name, null, capacity too small). */
