@@ -40,8 +40,12 @@ Relaxation times: tau_c,nm(x) = tau*_nm tau_ref (rho_ref / rho(x)) for Maxwell m
 (viscosity proportional to temperature, Sec. 4.2) or tau*_nm tau_ref without the density law;
 the discrete relaxation time is tau_nm = tau_c,nm + 1/2 (second-order time discretisation).
 
+ES-BGK (Model.es_b set): step 3 instead relaxes every order n >= 2 at the single rate 1/tau_20
+toward the local-frame coefficients of Holway's anisotropic Gaussian (``es_target``).
+
 Parity: pinned (conservation, equilibrium fixed point, BGK reduction against an independent
-regularised-BGK formula, single-mode decay, Rankine-Hugoniot steady shock).
+regularised-BGK formula, single-mode decay, Rankine-Hugoniot steady shock; for ES-BGK the
+target against direct numerical integration of the Gaussian, b = 0 against BGK, Pr = 1/(1-b)).
 """
 from __future__ import annotations
 
@@ -73,6 +77,7 @@ class Model:
     tau_star: dict = field(default_factory=lambda: dict(TAU_STAR_SMRT))
     rho_ref: float = 1.0
     maxwell_law: bool = True
+    es_b: float | None = None           # None: SMRT; else the ES-BGK model with parameter b
 
 
 @dataclass
@@ -185,6 +190,59 @@ def relax(d, N: int, tau):
     return out
 
 
+def es_target(d, N: int, rho, b: float):
+    """Local-frame coefficients (undivided, like d) of the ES-BGK target (Sec. 3, Eq. ES-BGK):
+    the Gaussian of covariance Lambda = theta delta + b sigma / rho. In the scaled variable
+    v = (xi - u)/sqrt(theta) its covariance is A = I + B, B = (b / rho) D2 with D2 the order-2
+    coefficient tensor of f (sigma = theta D2), and the Hermite coefficients of a Gaussian
+    follow from E[exp(t.v - |t|^2/2)] = exp(t.B.t / 2): the coefficient of t^beta / beta! is
+    the target's d_beta / rho. Only even orders are nonzero."""
+    al = alphas(N)
+    pos = {a: k for k, a in enumerate(al)}
+    ncell = d.shape[1]
+    # the quadratic form Q(t) = t.B.t / 2 as a monomial dictionary (exponent -> per-cell value)
+    Bf = {}
+    for k in range(3):
+        for l in range(3):
+            e = [0, 0, 0]
+            e[k] += 1
+            e[l] += 1
+            Bf[tuple(e)] = Bf.get(tuple(e), 0.0) + 0.5 * (b / rho) * d[pos[tuple(e)]]
+    out = np.zeros_like(d)
+    out[pos[(0, 0, 0)]] = rho
+    term = {(0, 0, 0): np.ones(ncell)}
+    for k in range(1, N // 2 + 1):
+        nxt = {}
+        for e1, c1 in term.items():
+            for e2, c2 in Bf.items():
+                e = tuple(x + y for x, y in zip(e1, e2))
+                nxt[e] = nxt.get(e, 0.0) + c1 * c2 / k        # Q^k / k! built as (Q^(k-1)/(k-1)!) Q / k
+        term = nxt
+        for e, c in term.items():
+            out[pos[e]] = rho * alpha_factorial(e) * c
+    return out
+
+
+def es_discrete_b(tau20, b: float):
+    """The ES parameter of the discrete-time scheme. The continuous model relaxes the stress
+    at (1 - b)/tau_c and the heat flux at 1/tau_c; the second-order scheme turns each such
+    continuous time into tau + 1/2 (as for every SMRT mode), so with one discrete rate 1/tau_20
+    (tau_20 = tau_c + 1/2) the target uses b' with (1 - b')/tau_20 = 1/(tau_c/(1 - b) + 1/2)."""
+    return 1.0 - (1.0 - b) * tau20 / (tau20 - 0.5 * b)
+
+
+def relax_es(d, N: int, tau20, rho, b: float):
+    """ES-BGK in the local frame: every order n >= 2 relaxes at the one discrete rate
+    1/tau_20 toward the ES target of parameter es_discrete_b(tau_20, b) (orders 0 and 1 are
+    the target's own)."""
+    target = es_target(d, N, rho, es_discrete_b(tau20, b))
+    out = d.copy()
+    sl = order_slices(N)
+    for n in range(2, N + 1):
+        out[sl[n]] = d[sl[n]] - (d[sl[n]] - target[sl[n]]) / tau20
+    return out
+
+
 # ---------------------------------------------------------------------------- step 5
 def rebuild(a, lat: Lattice, N: int):
     """f_i = w_i sum_{|alpha|<=N} a_alpha He_alpha(xi_i) / alpha!  (Eq. fi)."""
@@ -200,7 +258,10 @@ def collide(f, model: Model):
     lat, N = model.lat, model.N
     rho, u, theta = conserved(f, lat)
     d = local_direct(f, lat, N, u, theta)
-    d2 = relax(d, N, tau_discrete(model, rho))
+    if model.es_b is None:
+        d2 = relax(d, N, tau_discrete(model, rho))
+    else:
+        d2 = relax_es(d, N, tau_discrete(model, rho)[(2, 0)], rho, model.es_b)
     a2 = to_absolute(d2, N, u, theta)
     return rebuild(a2, lat, N)
 

@@ -259,3 +259,89 @@ def test_pull_cells_matches_stream(lats):
     full = S.stream(h, lat, geom).reshape(lat.q, -1)
     cells = rng.choice(5 * 6 * 7, size=20, replace=False)
     np.testing.assert_array_equal(S.pull_cells(h, lat, geom, cells), full[:, cells])
+
+
+# ---------------------------------------------------------------------------- ES-BGK
+def test_es_target_matches_gaussian_integration(lats):
+    """Sec. 3, Eq. ES-BGK: the target's local-frame Hermite coefficients equal rho E[He_beta(v)]
+    for v ~ N(0, A), A = I + (b/rho) D2, here integrated directly by a 3D Gauss-Hermite rule on
+    v = L z (A = L L^T) with numpy's own Hermite evaluation (no generating function)."""
+    from numpy.polynomial.hermite_e import hermeval
+    lat = lats["D3Q729"]
+    N, b = 5, -0.5
+    f, _ = _random_state(lat, N, ncell=2, eps=0.2)
+    rho, u, th = S.conserved(f, lat)
+    d = S.local_direct(f, lat, N, u, th)
+    got = S.es_target(d, N, rho, b)
+    al = H.multi_indices_upto(N)
+    pos = {a: k for k, a in enumerate(al)}
+    z, wz = hermegauss(12)
+    wz = wz / wz.sum()
+    Z = np.stack(np.meshgrid(z, z, z, indexing="ij"), axis=-1).reshape(-1, 3)
+    WZ = np.einsum("i,j,k->ijk", wz, wz, wz).ravel()
+    for c in range(2):
+        D2 = np.zeros((3, 3))
+        for k in range(3):
+            for l in range(3):
+                e = [0, 0, 0]
+                e[k] += 1
+                e[l] += 1
+                D2[k, l] = d[pos[tuple(e)], c]
+        A = np.eye(3) + (b / rho[c]) * D2
+        V = Z @ np.linalg.cholesky(A).T
+        for beta in al:
+            hv = np.ones(len(V))
+            for k in range(3):
+                hv = hv * hermeval(V[:, k], [0] * beta[k] + [1])
+            want = rho[c] * (WZ * hv).sum()
+            assert abs(got[pos[beta], c] - want) < 1e-12 * max(1.0, abs(want)), beta
+
+
+def test_es_b_zero_is_bgk(lats):
+    """ES-BGK with b = 0 is the BGK model: the regularised-BGK formula written without frames."""
+    lat = lats["D3Q729"]
+    N = 5
+    f, _ = _random_state(lat, N, eps=0.2)
+    tau_c = 0.9
+    model = S.Model(lat, N, tau_ref=tau_c, maxwell_law=False, es_b=0.0)
+    rho, u, th = S.conserved(f, lat)
+    feq = S.equilibrium(rho, u, th, lat, N)
+    al = H.multi_indices_upto(N)
+    He = H.he_multi(al, lat.xi)
+    fact = np.array([H.alpha_factorial(a) for a in al], dtype=float)
+    proj = lat.w[:, None] * (He / fact) @ (He.T @ (f - feq))
+    np.testing.assert_allclose(S.collide(f, model), feq + (1.0 - 1.0 / (tau_c + 0.5)) * proj, atol=1e-13)
+
+
+@pytest.mark.parametrize("b", [-0.5, 0.3])
+def test_es_prandtl_number_from_decay_rates(lats, b):
+    """Holway's model: Pr = 1/(1 - b) (2/3 at b = -1/2), read off the continuous relaxation
+    times of a shear and a heat-flux mode measured from one collision."""
+    lat = lats["D3Q729"]
+    N = 5
+    model = S.Model(lat, N, tau_ref=1.3, maxwell_law=False, es_b=b)
+    rng = np.random.default_rng(8)
+    rates = {}
+    for n, m in [(2, 0), (3, 1)]:
+        mode = H.components(_pure_mode(n, m, rng))
+        al = H.multi_indices_upto(N)
+        d = np.zeros((len(al), 1))
+        d[0, 0] = 1.0
+        k0 = [k for k, a in enumerate(al) if sum(a) == n and abs(mode[a]) > 1e-3][0]
+        for k, a in enumerate(al):
+            if sum(a) == n:
+                d[k, 0] = 1e-4 * mode[a]
+        f = S.rebuild(S.to_absolute(d, N, np.zeros((3, 1)), np.ones(1)), lat, N)
+        dh = S.local_direct(S.collide(f, model), lat, N, np.zeros((3, 1)), np.ones(1))
+        lam = dh[k0, 0] / d[k0, 0]
+        rates[(n, m)] = 1.0 / (1.0 - lam) - 0.5
+    # the order-4 part of the target is quadratic in the 1e-4 amplitude: Pr to ~1e-8
+    assert abs(rates[(2, 0)] / rates[(3, 1)] - 1.0 / (1.0 - b)) < 1e-7
+
+
+def test_es_collision_conserves(lats):
+    lat = lats["D3Q729"]
+    f, _ = _random_state(lat, 5, eps=0.2)
+    h = S.collide(f, S.Model(lat, 5, tau_ref=0.7, es_b=-0.5))
+    for a, b in zip(S.conserved(f, lat), S.conserved(h, lat)):
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-14)
