@@ -133,6 +133,22 @@ lb_status lb_set_relaxation(lb_ctx *ctx, const double *tau, int maxwell_molecule
  * Errors: LB_ERR_INVALID (bad instance; a single box accepts only -1), LB_ERR_CUDA. */
 lb_status lb_set_frame_shift(lb_ctx *ctx, int instance, int kx);
 
+/* Collision models of lb_set_collision_model. */
+#define LB_MODEL_SMRT 0   /* Eq. SMRT: each irreducible part (n, m) with its own time (default) */
+#define LB_MODEL_ES_BGK 1 /* Eq. ES-BGK: one time, target = Holway's ellipsoidal Gaussian    */
+
+/* lb_set_collision_model -- choose the collision model of one instance (-1 = all).
+ * LB_MODEL_ES_BGK (Sec. 3, Eq. ES-BGK; the paper notes that its covariance
+ * Lambda = theta delta + b sigma / rho is a weighted sum of two order-2 irreducible tensors):
+ * every order n >= 2 of the local-frame coefficients relaxes at the one discrete rate
+ * 1/tau_20 (tau_20 = the first time given to lb_set_relaxation, + 1/2, with its density law)
+ * toward the coefficients of that Gaussian, truncated at N. The discrete scheme uses
+ * b' = 1 - (1 - b) tau_20 / (tau_20 - b/2), which keeps the continuous model's stress rate
+ * (1 - b)/tau_c under the second-order discretisation, so Pr = 1/(1 - b) (2/3 at b = -1/2).
+ * Requires -1/2 <= b < 1. Tensor-product sets (D3Q729, D3Q4913) only. Synchronises.
+ * Errors: LB_ERR_INVALID (instance, model or b), LB_ERR_UNSUPPORTED (other sets), LB_ERR_CUDA. */
+lb_status lb_set_collision_model(lb_ctx *ctx, int instance, int model, double b);
+
 /* lb_fill_equilibrium -- f = order-N truncated Maxwellian of the given fields at every cell
  * (Sec. 3: f_i^eq is the truncated Hermite expansion of Eq. Maxwellian evaluated at xi_i,
  * built through Eq. fi). rho, theta: ncells doubles; u: 3*ncells doubles (row k = component

@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsmrt.so"
 LB_OK, LB_ERR_INVALID, LB_ERR_CUDA, LB_ERR_UNSTABLE, LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED, LB_ERR_NOMEM = range(7)
 LB_F64, LB_F32, LB_F32_CONS64 = 0, 1, 2
 LB_MOM_RHO, LB_MOM_U, LB_MOM_THETA, LB_MOM_SIGMA, LB_MOM_Q, LB_MOM_D = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+LB_MODEL_SMRT, LB_MODEL_ES_BGK = 0, 1
 LB_HEALTH_UNSTABLE, LB_HEALTH_TIMEOUT = 0x1, 0x2
 
 
@@ -38,6 +39,7 @@ SIGNATURES = {
     "lb_init_lattice": (c_int, [POINTER(c_void_p), POINTER(LbLatticeDesc), POINTER(LbGridDesc), c_int, c_int, c_void_p]),
     "lb_set_relaxation": (c_int, [c_void_p, POINTER(c_double), c_int, c_double, POINTER(LbState), POINTER(LbState), c_int]),
     "lb_set_frame_shift": (c_int, [c_void_p, c_int, c_int]),
+    "lb_set_collision_model": (c_int, [c_void_p, c_int, c_int, c_double]),
     "lb_fill_equilibrium": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lb_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "lb_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_uint]),

@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import (LB_F32, LB_F32_CONS64, LB_F64, LB_MOM_D, LB_MOM_Q, LB_MOM_RHO, LB_MOM_SIGMA,  # noqa: F401
-                   LB_MOM_THETA, LB_MOM_U, LbGridDesc, LbLatticeDesc, LbSchedule, LbState)
+                   LB_MODEL_ES_BGK, LB_MODEL_SMRT, LB_MOM_THETA, LB_MOM_U, LbGridDesc, LbLatticeDesc,
+                   LbSchedule, LbState)
 
 PRECISIONS = {"f64": LB_F64, "f32": LB_F32, "f32c64": LB_F32_CONS64}
 
@@ -172,6 +173,11 @@ def lb_set_relaxation(ctx: Context, tau, maxwell_molecule_law: bool = True, rho_
 
 def lb_set_frame_shift(ctx: Context, instance: int, kx: int):
     _check(_ffi.lib().lb_set_frame_shift(ctx.handle, int(instance), int(kx)), "lb_set_frame_shift")
+
+
+def lb_set_collision_model(ctx: Context, instance: int, model: int, b: float = 0.0):
+    _check(_ffi.lib().lb_set_collision_model(ctx.handle, int(instance), int(model), float(b)),
+           "lb_set_collision_model")
 
 
 def _ptr(t, dtype=None):

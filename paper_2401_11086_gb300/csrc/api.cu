@@ -428,6 +428,22 @@ extern "C" lb_status lb_set_frame_shift(lb_ctx *c, int instance, int kx) {
     return cuda_status(e);
 }
 
+extern "C" lb_status lb_set_collision_model(lb_ctx *c, int instance, int model, double b) {
+    if (!c || instance < -1 || instance >= c->batch) return LB_ERR_INVALID;
+    if (model != LB_MODEL_SMRT && model != LB_MODEL_ES_BGK) return LB_ERR_INVALID;
+    if (model == LB_MODEL_ES_BGK && !(b >= -0.5 && b < 1.0)) return LB_ERR_INVALID;
+    if (model == LB_MODEL_ES_BGK && c->kind < 2) return LB_ERR_UNSUPPORTED;
+    const int j0 = instance < 0 ? 0 : instance, j1 = instance < 0 ? c->batch : instance + 1;
+    for (int j = j0; j < j1; ++j) {
+        c->h_inst[j].model = model;
+        c->h_inst[j].es_b = model == LB_MODEL_ES_BGK ? b : 0.0;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * c->batch,
+                                    cudaMemcpyHostToDevice, c->view.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
+    return cuda_status(e);
+}
+
 extern "C" lb_status lb_fill_equilibrium(lb_ctx *c, void *f, const double *rho, const double *u,
                                          const double *theta) {
     if (!c || !f || !rho || !u || !theta) return LB_ERR_INVALID;

@@ -39,6 +39,8 @@ struct InstanceInfo {
     float tauAf[kMaxTau];  // the same in float, read by the float kernels
     float tauBf[kMaxTau];
     double dAdt, dBdt;     // d tauA / d tau_c and d tauB / d tau_c (adjoint)
+    int model;             // collision model: 0 SMRT, 1 ES-BGK (tensor-product sets)
+    double es_b;           // ES-BGK parameter b of the continuous model
 };
 
 template <class T>

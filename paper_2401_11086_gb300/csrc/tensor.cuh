@@ -277,9 +277,57 @@ struct TPCell {
         });
     }
 
+    // a5 for the ES-BGK model (Sec. 3, Eq. ES-BGK): every order n >= 2 relaxes at the one
+    // discrete rate 1/tau_20 toward the local-frame coefficients of Holway's Gaussian of
+    // covariance theta delta + b' sigma / rho. In divided form they are the monomial
+    // coefficients of rho exp(t.B.t / 2), B = (b'/rho) D2: order 2 is b' v2, order 4 is
+    // (b'^2 / (2 rho)) times the sum over ordered pairs of order-2 slots adding up to the slot,
+    // odd orders are zero. b' = 1 - (1 - b) tau_20 / (tau_20 - b/2) keeps the continuous stress
+    // rate (1 - b)/tau_c under the second-order scheme (tau -> tau + 1/2 per mode), so
+    // Pr = 1/(1 - b).
+    SMRT_D static void relax_es(T (&v)[M], T rho, T A, T B, T b) {
+        const T tau = fma(B, rho, A) * rcp(rho);
+        const T om = rcp(tau);
+        const T bp = T(1) - (T(1) - b) * tau * rcp(fma(T(-0.5), b, tau));
+        const T s = T(1) - om;
+        T t4[M];
+        static_for<M>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            if constexpr (mi_order(p) == 4) {
+                T acc = T(0);
+                static_for<M>([&](auto Q1s) {
+                    constexpr int q1 = decltype(Q1s)::value;
+                    if constexpr (mi_order(q1) == 2) {
+                        static_for<M>([&](auto Q2s) {
+                            constexpr int q2 = decltype(Q2s)::value;
+                            if constexpr (mi_order(q2) == 2 && mi_comp(q1, 0) + mi_comp(q2, 0) == mi_comp(p, 0) &&
+                                          mi_comp(q1, 1) + mi_comp(q2, 1) == mi_comp(p, 1))
+                                acc = fma(v[q1], v[q2], acc);
+                        });
+                    }
+                });
+                t4[p] = acc;
+            }
+        });
+        const T k4 = om * bp * bp * T(0.5) * rcp(rho);
+        const T s2 = fma(om, bp, s);
+        static_for<M>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            constexpr int n = mi_order(p);
+            if constexpr (n == 2)
+                v[p] *= s2;
+            else if constexpr (n == 4)
+                v[p] = fma(k4, t4[p], s * v[p]);
+            else if constexpr (n >= 3)
+                v[p] *= s;
+        });
+    }
+
     // a2, a4-a6 on the raw moments: R (in) -> rebuild coefficients P (out, same slots) with
-    // f'_i = w_i sum_gamma P_gamma e_i^gamma. Returns false when rho or theta is not positive.
-    SMRT_D static bool collide_moments(T (&R)[M], T c, const T *tauA, const T *tauB) {
+    // f'_i = w_i sum_gamma P_gamma e_i^gamma. model 1: ES-BGK with parameter es_b, else SMRT.
+    // Returns false when rho or theta is not positive.
+    SMRT_D static bool collide_moments(T (&R)[M], T c, const T *tauA, const T *tauB, int model = 0,
+                                       T es_b = T(0)) {
         T cp[N + 1];
         cp[0] = T(1);
         static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
@@ -313,12 +361,16 @@ struct TPCell {
         v[0] = rho;
         to_local_divided<N, T>(v, u, theta, thm1);
         // a5
-        T s[ntau(N)];
-        static_for<ntau(N)>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
-        });
-        static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
+        if (model == 1) {
+            relax_es(v, rho, tauA[0], tauB[0], es_b);
+        } else {
+            T s[ntau(N)];
+            static_for<ntau(N)>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
+            });
+            static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
+        }
         // a6
         const T sq = theta * rsq(theta);
         T sp[N + 1];
@@ -654,7 +706,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
         if (st + NS < S::kTotal) issue(st + NS);
     }
     if (active) {
-        const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in));
+        const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in), in.model, T(in.es_b));
         if (!ok) atomicOr(a.health, 1u);
         T *dst = fout + base + x;
         auto put = [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; };

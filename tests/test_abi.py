@@ -96,6 +96,7 @@ def test_validation_before_any_cuda_call(lib):
     assert lib.lb_step(None, None, None, 1) == 1
     assert lib.lb_moments(None, None, None, 1) == 1
     assert lib.lb_poll_status(None, None) == 1
+    assert lib.lb_set_collision_model(None, -1, 1, -0.5) == 1
     assert lib.lb_cells(None) == 0
 
 
