@@ -284,6 +284,22 @@ int lb_num_moment_rows(const lb_ctx *ctx, unsigned which_mask);
 lb_status lb_lattice_named(const char *name, int8_t *e_out, double *w_out, double *c_out,
                            int *q_out, int *degree_out, int capacity);
 
+/* lb_hermite_convergence -- the convergence study of Appendix B (Eq. fexp): for each of npts
+ * points (theta[p] > 0, u[p]) the smallest order N <= nmax whose truncated Hermite expansion
+ * f_N = omega(xi) sum_{n<=N} a^(n) He_n(xi)/n! of the 1D Maxwellian of temperature theta and
+ * velocity u has L1 error int |f - f_N| dxi < tol (the paper's figure uses tol = 0.01).
+ * order[p] = that N, or nmax + 1 when no order up to nmax reaches tol (-1 for a point with
+ * theta <= 0 or a non-finite value); err[p] = the error at order[p] (at nmax when not reached;
+ * NaN for invalid points). The integral is composite Simpson on 4097 points of [-L, L],
+ * L = max(|u| + 12 sqrt(theta), 2 sqrt(nmax + 1) + 10); a^(n) and He_n come from their
+ * recurrences scaled by sqrt(n!). theta, u (npts doubles), order (npts ints) and err (npts
+ * doubles) are device memory; asynchronous on cudaStream_t stream; no context needed.
+ * Errors: LB_ERR_INVALID (npts < 0, nmax outside 0..LB_HERMITE_MAX_ORDER, tol <= 0, null
+ * pointers), LB_ERR_CUDA. */
+#define LB_HERMITE_MAX_ORDER 200
+lb_status lb_hermite_convergence(const double *theta, const double *u, int npts, double tol, int nmax,
+                                 int *order, double *err, void *stream);
+
 /* lb_rankine_hugoniot -- end states of a normal shock (Eq. rankine, temperature ratio read
  * with Ma^2 in the denominator) for upstream Mach number Ma, ratio of specific heats gamma,
  * upstream rho1 and theta1; velocities in the shock frame, along +x (host memory out). */

@@ -8,4 +8,4 @@ from .api import (LB_F32, LB_F32_CONS64, LB_F64, LB_MOM_D, LB_MOM_Q, LB_MOM_RHO,
                   lb_rankine_hugoniot, lb_set_frame_shift, lb_shock_frame,
                   lb_autotune, lb_get_schedule, lb_set_schedule, lb_step_graph,
                   lb_test_barrier_timeout, lb_set_relaxation, lb_step,
-                  LB_MODEL_ES_BGK, LB_MODEL_SMRT, lb_set_collision_model)
+                  LB_MODEL_ES_BGK, LB_MODEL_SMRT, lb_set_collision_model, lb_hermite_convergence)

@@ -40,6 +40,7 @@ SIGNATURES = {
     "lb_set_relaxation": (c_int, [c_void_p, POINTER(c_double), c_int, c_double, POINTER(LbState), POINTER(LbState), c_int]),
     "lb_set_frame_shift": (c_int, [c_void_p, c_int, c_int]),
     "lb_set_collision_model": (c_int, [c_void_p, c_int, c_int, c_double]),
+    "lb_hermite_convergence": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_void_p]),
     "lb_fill_equilibrium": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lb_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "lb_moments": (c_int, [c_void_p, c_void_p, c_void_p, c_uint]),

@@ -175,6 +175,24 @@ def lb_set_frame_shift(ctx: Context, instance: int, kx: int):
     _check(_ffi.lib().lb_set_frame_shift(ctx.handle, int(instance), int(kx)), "lb_set_frame_shift")
 
 
+def lb_hermite_convergence(theta, u, tol: float = 0.01, nmax: int = 99, stream=None):
+    """Appendix B study on the GPU: (order int32, err float64) tensors for the points
+    (theta[p], u[p]) given as float64 CUDA tensors of one shape."""
+    import torch
+    th = theta.contiguous().to(torch.float64)
+    uu = u.contiguous().to(torch.float64)
+    if th.shape != uu.shape or th.device.type != "cuda" or uu.device != th.device:
+        raise ValueError("theta and u must be CUDA tensors of one shape")
+    order = torch.empty(th.shape, dtype=torch.int32, device=th.device)
+    err = torch.empty(th.shape, dtype=torch.float64, device=th.device)
+    stream = torch.cuda.current_stream(th.device) if stream is None else stream
+    _check(_ffi.lib().lb_hermite_convergence(c_void_p(th.data_ptr()), c_void_p(uu.data_ptr()), int(th.numel()),
+                                             float(tol), int(nmax), c_void_p(order.data_ptr()),
+                                             c_void_p(err.data_ptr()), c_void_p(stream.cuda_stream)),
+           "lb_hermite_convergence")
+    return order, err
+
+
 def lb_set_collision_model(ctx: Context, instance: int, model: int, b: float = 0.0):
     _check(_ffi.lib().lb_set_collision_model(ctx.handle, int(instance), int(model), float(b)),
            "lb_set_collision_model")

@@ -97,6 +97,9 @@ def test_validation_before_any_cuda_call(lib):
     assert lib.lb_moments(None, None, None, 1) == 1
     assert lib.lb_poll_status(None, None) == 1
     assert lib.lb_set_collision_model(None, -1, 1, -0.5) == 1
+    assert lib.lb_hermite_convergence(None, None, -1, 0.01, 10, None, None, None) == 1
+    assert lib.lb_hermite_convergence(None, None, 4, 0.01, 500, None, None, None) == 1
+    assert lib.lb_hermite_convergence(None, None, 0, 0.01, 10, None, None, None) == 0
     assert lib.lb_cells(None) == 0
 
 
