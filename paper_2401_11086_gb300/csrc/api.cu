@@ -321,6 +321,11 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     }
+    // D3Q729 problems of at most 12 cells per SM take one block per cell (measured crossover)
+    if (e == cudaSuccess && c->kind == 2 && (long long)ncells <= 12LL * c->num_sms) {
+        c->sched.tile_width = 1;
+        v.tile_width = 1;
+    }
     if (e != cudaSuccess) {
         free_tables(c);
         delete c;
@@ -503,7 +508,9 @@ extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
 
 extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
     if (!c || !s) return LB_ERR_INVALID;
-    if (s->tile_width != 32 && s->tile_width != 64 && s->tile_width != 128) return LB_ERR_INVALID;
+    const bool cell_blocks = s->tile_width == 1;  // D3Q729: one cell per block, one launch per step
+    if (s->tile_width != 32 && s->tile_width != 64 && s->tile_width != 128 && !cell_blocks) return LB_ERR_INVALID;
+    if (cell_blocks && (c->kind != 2 || s->persistent)) return LB_ERR_UNSUPPORTED;
     if (s->blocks_per_sm < 0 || (s->persistent != 0 && s->persistent != 1)) return LB_ERR_INVALID;
     if (!c->view.line) {  // the box kernel has one fixed launch shape
         if (s->persistent || s->tile_width != kTile) return LB_ERR_UNSUPPORTED;
@@ -540,12 +547,12 @@ extern "C" lb_status lb_autotune(lb_ctx *c, void *fa, void *fb, int trial_steps,
     lb_status st = check_pair(c, fa, fb, 2);
     if (st != LB_OK || trial_steps < 1 || !best) return st != LB_OK ? st : LB_ERR_INVALID;
     std::vector<lb_schedule> cand;
-    const int widths[3] = {32, 64, 128};
-    const int nwidths = c->view.line ? 3 : 1;
+    const int widths[4] = {32, 64, 128, 1};
+    const int nwidths = c->view.line ? (c->kind == 2 ? 4 : 3) : 1;
     for (int wi = 0; wi < nwidths; ++wi) {
         const int width = c->view.line ? widths[wi] : kTile;
         cand.push_back(lb_schedule{width, 0, 0, 0.0});  // one launch per step
-        if (!c->view.line) continue;
+        if (!c->view.line || width == 1) continue;
         const lb_schedule probe{width, 0, 1, 0.0};
         if (lb_set_schedule(c, &probe) != LB_OK) continue;
         const int occ = c->ks->occupancy(c->view);

@@ -227,6 +227,17 @@ inline int tp_blocks(const CtxView &v) {
 template <class L1, int N, class T>
 cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
     const TPArgs<T> a = make_tp_args<T>(v, fin, fout);
+    if (v.tile_width == 1) {  // one cell per block (D1Q9-P1 sets only: its tables fit in 48 KB)
+        if constexpr (L1::Q1 == 9) {
+            if (v.fixedx)
+                tp_step_cell_kernel<L1, N, T, true><<<v.ntiles * 32, 128, 0, v.stream>>>(a);
+            else
+                tp_step_cell_kernel<L1, N, T, false><<<v.ntiles * 32, 128, 0, v.stream>>>(a);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidConfiguration;
+        }
+    }
     const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
     if (v.fixedx) {
         const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true>, L1, T>();

@@ -799,6 +799,112 @@ __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a,
 }
 
 // ------------------------------------------------------------------------------ kernels
+// ------------------------------------------------------------------ one cell per block
+// For problems too small to fill the GPU with one thread per cell (the paper's own runs are
+// single shocks of 100 cells), each block takes one cell: its d^3 pulled populations go to
+// shared memory, the x-rows and the raw moments are summed by the block's threads, the
+// moment-space steps run in warp 0 (every lane the same, lane 0 writes), and the rebuild is
+// spread over the x-rows again. Block b takes cell x0 + b % 32 of the 32-cell tile b / 32.
+template <class L1, int N, class T>
+struct TPCellShared {
+    static constexpr int Q1 = L1::Q1, P2 = Q1 * Q1, Q = P2 * Q1, M = nmom(N);
+    T f[Q];             // pulled populations, library order
+    T g[P2][N + 1];     // x-row sums g_j of row (b, c) = b + d c
+    T ep[Q1][N + 1];    // e_a^j
+    T R[M];             // raw moments, then the rebuild coefficients
+};
+
+template <class L1, int N, class T, bool FixedX>
+__global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
+    using C = TPCell<L1, N, T>;
+    using SH = TPCellShared<L1, N, T>;
+    constexpr int Q1 = SH::Q1, P2 = SH::P2, Q = SH::Q, M = SH::M;
+    __shared__ TPTables<L1, T> s;
+    __shared__ SH sh;
+    tp_load_tables<L1>(a, s);
+    const int tid = threadIdx.x;
+    const int2 tile = a.tiles[blockIdx.x >> 5];
+    const InstanceInfo &in = a.inst[tile.x];
+    const int x = tile.y + int(blockIdx.x & 31u), L = in.nx, kx = in.kx;
+    if (x >= L) return;  // the whole block: no barrier follows for it
+    const long long base = in.cell_off;
+    const T *gl = a.ghosts + (long long)tile.x * 2 * Q;
+    const T *gr = gl + Q;
+    for (int q = tid; q < Q1 * (N + 1); q += blockDim.x) {
+        const int av = q / (N + 1), j = q % (N + 1);
+        T p = T(1);
+        for (int r = 0; r < j; ++r) p *= s.e[av];
+        sh.ep[av][j] = p;
+    }
+    // a1: pull every population of the cell
+    for (int i = tid; i < Q; i += blockDim.x) {
+        const int t = x - e1<L1>(i % Q1) - kx;
+        T v;
+        if (FixedX && t < 0)
+            v = gl[i];
+        else if (FixedX && t >= L)
+            v = gr[i];
+        else
+            v = a.fin[(long long)s.plane[i] * a.stride + base + (FixedX ? t : wrap(t, L))];
+        sh.f[i] = v;
+    }
+    __syncthreads();
+    // a3, x first: one x-row per thread
+    for (int row = tid; row < P2; row += blockDim.x) {
+        const T *fr = sh.f + row * Q1;
+        T g[N + 1];
+        C::xrow([&](auto A) -> T { return fr[decltype(A)::value]; }, g);
+        static_for<N + 1>([&](auto J) { sh.g[row][decltype(J)::value] = g[decltype(J)::value]; });
+    }
+    __syncthreads();
+    // ... then y and z: R_(j,k,l) = sum_(b,c) g_(b,c)j e_b^k e_c^l, one moment per thread
+    for (int m = tid; m < M; m += blockDim.x) {
+        const int j = mi_comp(m, 0), k = mi_comp(m, 1), l = mi_comp(m, 2);
+        T acc = T(0);
+        for (int c = 0; c < Q1; ++c) {
+            T ac = T(0);
+            for (int b = 0; b < Q1; ++b) ac = fma(sh.g[b + Q1 * c][j], sh.ep[b][k], ac);
+            acc = fma(ac, sh.ep[c][l], acc);
+        }
+        sh.R[m] = acc;
+    }
+    __syncthreads();
+    // a2, a4-a6 in warp 0
+    if (tid < 32) {
+        T R[M];
+        static_for<M>([&](auto G) { R[decltype(G)::value] = sh.R[decltype(G)::value]; });
+        const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in), in.model, T(in.es_b));
+        __syncwarp();
+        if (tid == 0) {
+            if (!ok) atomicOr(a.health, 1u);
+            static_for<M>([&](auto G) { sh.R[decltype(G)::value] = R[decltype(G)::value]; });
+        }
+    }
+    __syncthreads();
+    // a7 + a8: one x-row per thread, Pb_j = sum_(k,l) P_(j,k,l) e_b^k e_c^l
+    T *dst = a.fout + base + x;
+    auto put = [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; };
+    for (int row = tid; row < P2; row += blockDim.x) {
+        const int b = row % Q1, c = row / Q1;
+        T Pb[N + 1];
+        static_for<N + 1>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            T acc = T(0);
+            static_for<N + 1 - j>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                T ac = T(0);
+                static_for<N + 1 - j - k>([&](auto Lm) {
+                    constexpr int l = decltype(Lm)::value;
+                    ac = fma(sh.R[mi_pos(j, k, l)], sh.ep[c][l], ac);
+                });
+                acc = fma(ac, sh.ep[b][k], acc);
+            });
+            Pb[j] = acc;
+        });
+        C::template emit_x<T>(Pb, s.w[b] * s.w[c], s.w, row * Q1, put);
+    }
+}
+
 // lb_moments of the pulled (pre-collision) populations.
 template <class L1, int N, class T>
 __global__ void __launch_bounds__(128) tp_moments_kernel(TPArgs<T> a, double *out, long long ncells,

@@ -78,7 +78,8 @@ def _batch(olat, d, N, prec, tau_star=None, ratios=shocks.TAU_RATIOS_SMRT):
 
 @pytest.mark.parametrize("N", [4, 5])
 @pytest.mark.parametrize("table", ["smrt", "shakhov", "reduced"])
-def test_table3_shocks_match_oracle(lat, N, table):
+@pytest.mark.parametrize("width", [1, 64])
+def test_table3_shocks_match_oracle(lat, N, table, width):
     """FP64, the three Table 3 rows (Ma 1.5/3/5, theta1 = 0.714/0.333/0.167, k_x = 2) in one
     batch from the step initial condition, 12 steps, each instance vs its own oracle run;
     SMRT, Shakhov and the 'reduced' tau_41 = tau_42 table of Sec. 4.3."""
@@ -88,6 +89,7 @@ def test_table3_shocks_match_oracle(lat, N, table):
     ratios = {"smrt": shocks.TAU_RATIOS_SMRT, "shakhov": shocks.TAU_RATIOS_SHAKHOV,
               "reduced": shocks.TAU_RATIOS_REDUCED}[table]
     ctx, params, cases, hs = _batch(olat, d, N, "f64", star, ratios)
+    P.lb_set_schedule(ctx, width, 0, 0)   # one block per cell, or warps of 32-cell tiles
     for p, case in zip(params, cases):
         assert p["kx"] == case.k == 2
         np.testing.assert_allclose(p["taus"], _tau(case.model), rtol=1e-14)
@@ -136,7 +138,8 @@ def test_moments_match_oracle(lat):
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
-def test_periodic_line_matches_oracle(lat, prec, tol):
+@pytest.mark.parametrize("width", [1, 64])
+def test_periodic_line_matches_oracle(lat, prec, tol, width):
     """Periodic line of 133 cells (a ragged 5-cell tail), shift 2, perturbed populations,
     1 and 4 steps."""
     olat, d, idx = lat
@@ -150,6 +153,7 @@ def test_periodic_line_matches_oracle(lat, prec, tol):
     geom = OS.Geometry(shape=(1, 1, nx), shift=shift)
     ctx = P.lb_init_lattice(_desc(d, shift), nx, N=N, precision=prec)
     P.lb_set_relaxation(ctx, _tau(model), True, 1.0)
+    P.lb_set_schedule(ctx, width, 0, 0)
     fa = upload(ctx, f0, idx)
     h = download(ctx, fa, idx).reshape(f0.shape)     # start from the stored (rounded) state
     for nsteps in (1, 4):
@@ -170,7 +174,7 @@ def test_schedules_and_graph_agree(lat):
     f0 = _upload_batch(ctx, d, idx, hs)
     runs = []
     for mode, sched in [("step", (128, 0, 0)), ("step", (32, 0, 0)), ("step", (64, 0, 0)),
-                        ("step", (64, 1, 1)), ("graph", (32, 2, 1))]:
+                        ("step", (64, 1, 1)), ("graph", (32, 2, 1)), ("step", (1, 0, 0))]:
         P.lb_set_schedule(ctx, *sched)
         fa, fb = f0.clone(), ctx.new_state()
         out = P.lb_step_graph(ctx, fa, fb, 12) if mode == "graph" else P.lb_step(ctx, fa, fb, 12)
@@ -181,6 +185,8 @@ def test_schedules_and_graph_agree(lat):
     assert torch.equal(runs[4], runs[3])
     scale = runs[0].abs().max()
     assert ((runs[3] - runs[0]).abs().max() / scale).item() < 1e-14
+    # one block per cell sums in another order
+    assert ((runs[5] - runs[0]).abs().max() / scale).item() < 1e-13
 
 
 def test_caller_velocity_order_is_free(lat):
@@ -321,11 +327,13 @@ def test_paper_configuration_ma7_n5_against_golden(lat17):
 
 # ------------------------------------------------------------------ ES-BGK target (Sec. 3)
 @pytest.mark.parametrize("b", [-0.5, 0.4])
-def test_es_bgk_table3_matches_oracle(lat, b):
+@pytest.mark.parametrize("width", [1, 64])
+def test_es_bgk_table3_matches_oracle(lat, b, width):
     """FP64 ES-BGK (Eq. ES-BGK, one relaxation time, Holway's Gaussian target) on the three
     Table 3 rows, N = 5, 12 steps, each instance vs the oracle's ES-BGK run."""
     olat, d, idx = lat
     ctx, params, cases, hs = _batch(olat, d, 5, "f64")
+    P.lb_set_schedule(ctx, width, 0, 0)
     P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, b)
     fa = _upload_batch(ctx, d, idx, hs)
     out = P.lb_step(ctx, fa, ctx.new_state(), 12)
