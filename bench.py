@@ -323,13 +323,17 @@ TP_FP64_FLOP_PER_CELL = 15301.0
 FP64_PEAK_GFLOPS = 1250.0
 
 
-def table3_instances(rank: int, count: int = 512):
-    """The D3Q729 workload of one rank: count shocks cycling over Table 3's rows (Ma 1.5, 3, 5
-    with their theta1), lengths 100..400 cells drawn with seed 11086 + rank."""
+def table3_instances(rank: int, count: int = 512, length: int = 0):
+    """The D3Q729 workload of one rank: count shocks cycling over Table 3's rows (Ma 3, 1.5, 5
+    with their theta1), lengths 100..400 cells drawn with seed 11086 + rank, or all `length`
+    cells when given (a single shock is then the paper's Ma = 3 run)."""
     import numpy as np
     from paper_2401_11086_gb300 import shocks
-    machs = [(1.5, 3.0, 5.0)[j % 3] for j in range(count)]
-    lengths = np.random.default_rng(11086 + rank).integers(100, 401, count)
+    machs = [(3.0, 1.5, 5.0)[j % 3] for j in range(count)]
+    if length > 0:
+        lengths = np.full(count, length)
+    else:
+        lengths = np.random.default_rng(11086 + rank).integers(100, 401, count)
     return machs, lengths, [shocks.TABLE3_THETA1[m] for m in machs]
 
 
@@ -370,13 +374,13 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    machs, lengths, theta1 = table3_instances(rank)
+    machs, lengths, theta1 = table3_instances(rank, args.instances, args.length)
     d = P.lb_lattice_named("D3Q729")
     stream = torch.cuda.current_stream()
     prec = args.precision
     ctx, f0, _ = shocks.setup_batch(d, 5, machs, lengths, precision=prec, width=0.0, theta1=theta1,
                                     stream=stream)
-    P.lb_set_schedule(ctx, 64, 0, 0)
+    sched = P.lb_get_schedule(ctx)   # the library's choice for this size
     fa, fb = f0, ctx.new_state()
     cur = P.lb_step(ctx, fa, fb, args.warmup)
     other = fb if cur is fa else fa
@@ -384,11 +388,19 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     if dist:
         dist.barrier()
     K = args.steps
+    cells = int(sum(lengths))
+    q = 729
+    elem = 8 if prec == "f64" else 4
+    # states that fit in the 129 MB L2 are flushed (256 MB write) before every timed step
+    small = 2 * q * elem * cells < 129e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f0.device) if small else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     for i in range(K):
+        if small:
+            flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
         cur = P.lb_step(ctx, cur, other, 1)
         ev[i][1].record(stream)
@@ -399,9 +411,6 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     st, flags = P.lb_poll_status(ctx)
     if st != 0:
         raise SystemExit(f"health word reports status {st} (flags {flags})")
-    cells = int(sum(lengths))
-    q = 729
-    elem = 8 if prec == "f64" else 4
     kern_ms = ms / K
     rate, ms = job_rate(cells * q * K, ms, dist)
     if rank != 0:
@@ -431,9 +440,9 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": f"table3_d3q729_n5_{prec}", "instances_per_gpu": len(machs),
                        "cells_per_gpu": cells, "velocities": q, "hermite_order": 5,
-                       "state_bytes": elem * int(ctx.state_elems),
-                       "l2": "inputs larger than L2" if q * elem * cells > 129e6 else
-                             "inputs smaller than L2 (steps timed one by one)"},
+                       "state_bytes": elem * int(ctx.state_elems), "schedule": sched,
+                       "l2": "L2 flushed (256 MB write) before every timed step" if small else
+                             "inputs larger than L2"},
             "roofline": roof, "cpu_baseline": cpu, "gpu_launches": K, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -452,6 +461,9 @@ def main():
                          "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
                     help="table3 workload only")
+    ap.add_argument("--instances", type=int, default=512, help="table3 workload: number of shocks")
+    ap.add_argument("--length", type=int, default=0,
+                    help="table3 workload: cells per shock (0: 100..400 by seed)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
