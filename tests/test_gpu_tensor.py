@@ -374,3 +374,22 @@ def test_es_bgk_periodic_f32_and_model_switch(lat):
     want = OS.step(h0, model, geom)
     got = download(ctx, P.lb_step(ctx, fa.clone(), ctx.new_state(), 1), idx)
     assert np.abs(got - want.reshape(olat.q, -1)).max() / np.abs(want).max() < 2e-6
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable(lat):
+    """D3Q729 persistent launch whose grid barrier can never complete: every block gives up
+    after its bounded wait, the health word says LB_HEALTH_TIMEOUT, and the context keeps
+    working afterwards (the step then matches a fresh per-step run)."""
+    olat, d, idx = lat
+    ctx, params, cases, hs = _batch(olat, d, 5, "f64")
+    f0 = _upload_batch(ctx, d, idx, hs)
+    P.lb_set_schedule(ctx, 64, 1, 1)
+    P.lb_test_barrier_timeout(ctx, f0.clone(), ctx.new_state())
+    st, flags = P.lb_poll_status(ctx)
+    assert st == 4 and flags & 2
+    a = P.lb_step(ctx, f0.clone(), ctx.new_state(), 3)
+    st, flags = P.lb_poll_status(ctx)
+    assert st == 0 and flags == 0
+    P.lb_set_schedule(ctx, 64, 0, 0)
+    b = P.lb_step(ctx, f0.clone(), ctx.new_state(), 3)
+    assert ((a - b).abs().max() / b.abs().max()).item() < 1e-14
