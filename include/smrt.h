@@ -188,8 +188,8 @@ typedef struct {
 lb_status lb_set_schedule(lb_ctx *ctx, const lb_schedule *schedule);
 lb_status lb_get_schedule(const lb_ctx *ctx, lb_schedule *schedule);
 
-/* lb_autotune -- time every candidate schedule (tile widths 32/64/128, one launch per step or
- * persistent with 1, 2, 4 or all resident blocks per SM) for trial_steps steps on the states
+/* lb_autotune -- time every candidate schedule (tile widths 32/64/128, and 1 on D3Q729; one
+ * launch per step or persistent with 1, 2, 4 or all resident blocks per SM) for trial_steps steps on the states
  * f_a / f_b (which it ADVANCES: pass copies), apply the fastest and return it in *best with
  * its ms_per_step. Synchronises. Errors: as lb_step, LB_ERR_CUDA. */
 lb_status lb_autotune(lb_ctx *ctx, void *f_a, void *f_b, int trial_steps, lb_schedule *best);
@@ -197,7 +197,9 @@ lb_status lb_autotune(lb_ctx *ctx, void *f_a, void *f_b, int trial_steps, lb_sch
 /* lb_step_graph -- lb_step of a 1D-line context as a replay of a CUDA graph holding one
  * persistent launch of nsteps steps (captured on first use for this (f_a, f_b, nsteps,
  * schedule) and cached in the context; capture needs no allocation of device memory). Same
- * buffer convention as lb_step. Errors: as lb_step, LB_ERR_UNSUPPORTED (box), LB_ERR_CUDA. */
+ * buffer convention as lb_step. Errors: as lb_step, LB_ERR_UNSUPPORTED (box, a D3Q729 context
+ * on its one-cell-per-block schedule, or a persistent kernel that cannot be resident),
+ * LB_ERR_CUDA. */
 lb_status lb_step_graph(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 
 /* lb_test_barrier_timeout -- failure-detection test of the persistent launch: runs two steps

@@ -473,11 +473,13 @@ lb_status check_pair(const lb_ctx *c, const void *fa, const void *fb, int nsteps
 // grid of the persistent launch: blocks_per_sm (0 = as many as fit) on every SM, at most one
 // block per tile
 long long persistent_grid(const lb_ctx *c) {
+    // blocks with work: one per tile, or per tile_width / 32 tiles on tensor-product sets
+    // (whose one-cell-per-block schedule, tile width 1, has no persistent form)
+    const long long wpb = c->kind >= 2 ? c->view.tile_width / 32 : 1;
+    if (wpb < 1) return 0;
     const int occ = c->ks->occupancy(c->view);
     if (occ < 1) return 0;
     const int bps = c->sched.blocks_per_sm > 0 ? std::min(c->sched.blocks_per_sm, occ) : occ;
-    // blocks with work: one per tile, or per tile_width / 32 tiles on tensor-product sets
-    const long long wpb = c->kind >= 2 ? c->view.tile_width / 32 : 1;
     const long long needed = (c->view.ntiles + wpb - 1) / wpb;
     return std::max(1LL, std::min((long long)bps * c->num_sms, needed));
 }
@@ -613,7 +615,7 @@ extern "C" lb_status lb_test_barrier_timeout(lb_ctx *c, void *fa, void *fb) {
 extern "C" lb_status lb_step_graph(lb_ctx *c, void *fa, void *fb, int nsteps) {
     const lb_status st = check_pair(c, fa, fb, nsteps);
     if (st != LB_OK) return st;
-    if (!c->view.line) return LB_ERR_UNSUPPORTED;
+    if (!c->view.line || persistent_grid(c) < 1) return LB_ERR_UNSUPPORTED;
     const bool same = c->graph && c->graph_fa == fa && c->graph_fb == fb && c->graph_steps == nsteps &&
                       c->graph_sched.tile_width == c->sched.tile_width &&
                       c->graph_sched.blocks_per_sm == c->sched.blocks_per_sm;

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 #include "tensor.cuh"
 
@@ -209,11 +211,20 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
 }
 
 // The warp-staged kernels may take more than the default 48 KB of dynamic shared memory:
-// raise the limit of each instantiation to what a 128-thread block needs (once per process).
+// raise the limit of each instantiation to what a 128-thread block needs, once per device
+// (the attribute belongs to the device the call is made on).
 template <auto Kernel, class L1, class T>
 cudaError_t tp_smem_limit() {
-    static const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      int(TPWarpStage<L1, T>::bytes(128)));
+    constexpr int kDevices = 64;
+    static std::atomic<int> state[kDevices];  // 0 not set, 1 set, 2 failed
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+    const int s = state[dev].load(std::memory_order_acquire);
+    if (s == 1) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TPWarpStage<L1, T>::bytes(128)));
+    state[dev].store(e == cudaSuccess ? 1 : 2, std::memory_order_release);
     return e;
 }
 

@@ -393,3 +393,19 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable(lat):
     P.lb_set_schedule(ctx, 64, 0, 0)
     b = P.lb_step(ctx, f0.clone(), ctx.new_state(), 3)
     assert ((a - b).abs().max() / b.abs().max()).item() < 1e-14
+
+
+def test_graph_needs_a_persistent_schedule(lat):
+    """A small D3Q729 context starts on the one-cell-per-block schedule, which has no
+    persistent form: the graph path refuses it instead of launching."""
+    olat, d, idx = lat
+    ctx, f0, _ = shocks.setup_batch(d, 5, [3.0], [100], precision="f64", width=0.0, theta1=[0.333])
+    assert P.lb_get_schedule(ctx)["tile_width"] == 1
+    with pytest.raises(P.SmrtError) as e:
+        P.lb_step_graph(ctx, f0.clone(), ctx.new_state(), 4)
+    assert e.value.status == 5
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(ctx, 1, 0, 1)
+    P.lb_set_schedule(ctx, 32, 1, 1)
+    out = P.lb_step_graph(ctx, f0.clone(), ctx.new_state(), 4)
+    assert P.lb_poll_status(ctx)[0] == 0 and torch.isfinite(out).all()
