@@ -21,6 +21,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "moment_tables.cuh"
 
 namespace smrt {
 
@@ -393,6 +394,151 @@ struct TPCell {
         binomial_divided<N, T>(v, G);
         v[0] = rhom1;  // deviation from the coefficients of w_i
         to_rebuild(v, c, R);
+        return ok;
+    }
+
+    // The steps of collide_moments (a2, a4-a6) with one cell's coefficients spread over the 32
+    // lanes of a warp: lane l owns slots l and l + 32, each step reads the whole vector from
+    // shared memory and writes its own slots (the per-slot constants come from MomentTables).
+    // Executing the single-thread version on every lane would spend a full warp's FP64 issue
+    // on each scalar operation. R (shared, M values): raw moments in, rebuild coefficients out;
+    // w (shared, M values) and gs (shared, 3 (N + 1) values): scratch. Every lane calls it.
+    SMRT_D static bool collide_moments_lanes(const MomentSmem<N, double> &tb, T *R, T *w, T *gs, T c, const T *tauA,
+                                             const T *tauB, int model, T es_b) {
+        const int lane = threadIdx.x & 31;
+        const int pa = lane, pb = lane + 32;
+        const bool two = pb < M;
+        // the lane's slots: components and orders in registers
+        const int ca[3] = {tb.c[pa][0], tb.c[pa][1], tb.c[pa][2]};
+        const int cb[3] = {two ? tb.c[pb][0] : 0, two ? tb.c[pb][1] : 0, two ? tb.c[pb][2] : 0};
+        const int oa = tb.c[pa][3], ob = two ? tb.c[pb][3] : 0;
+        auto ipow_t = [](T x, int e) {
+            T r = T(1);
+            for (int i = 0; i < e; ++i) r *= x;
+            return r;
+        };
+        auto axis_pass = [&](const T *src, T *dst, int k) {  // dst = T_k src (one binomial axis)
+            auto one = [&](int p, const int (&cc)[3]) {
+                const int ak = cc[k];
+                T acc = src[p];
+                for (int b = 0; b < ak; ++b) {
+                    const int q = k == 0 ? mi_pos(b, cc[1], cc[2]) : (k == 1 ? mi_pos(cc[0], b, cc[2]) : mi_pos(cc[0], cc[1], b));
+                    acc = fma(gs[k * (N + 1) + ak - b], src[q], acc);
+                }
+                dst[p] = acc;
+            };
+            one(pa, ca);
+            if (two) one(pb, cb);
+            __syncwarp();
+        };
+        // Rc = c^|gamma| R
+        w[pa] = R[pa] * ipow_t(c, oa);
+        if (two) w[pb] = R[pb] * ipow_t(c, ob);
+        __syncwarp();
+        // a2 (every lane): rho - 1 = Rc_0, rho u = Rc_1, E - 3 = tr Rc_2
+        const T rhom1 = w[0];
+        const T rho = T(1) + rhom1;
+        const T ir = rcp(rho);
+        const T u0 = w[mi_pos(1, 0, 0)] * ir, u1 = w[mi_pos(0, 1, 0)] * ir, u2 = w[mi_pos(0, 0, 1)] * ir;
+        const T uu = u0 * u0 + u1 * u1 + u2 * u2;
+        const T thm1 = (w[mi_pos(2, 0, 0)] + w[mi_pos(0, 2, 0)] + w[mi_pos(0, 0, 2)] - T(3) * rhom1 - rho * uu) * ir *
+                       T(1.0 / 3.0);
+        const T theta = T(1) + thm1;
+        const bool ok = (rho > T(0)) && (theta > T(0));
+        // ta = hdiv Rc (into R), full a_0 = rho
+        auto hd_row = [&](int p) {
+            T acc = T(0);
+            for (int i = 0; i < tb.hd_n[p]; ++i) acc = fma(tb.hd_val[p][i], w[tb.hd_col[p][i]], acc);
+            R[p] = p == 0 ? rho : acc;
+        };
+        hd_row(pa);
+        if (two) hd_row(pb);
+        // a4: T(-u, 2 - theta) then theta^(-|beta|/2)
+        if (lane < 3) {
+            T G[N + 1];
+            maxwell_divided<N, T>(G, lane == 0 ? -u0 : (lane == 1 ? -u1 : -u2), -thm1);
+            for (int j = 0; j <= N; ++j) gs[lane * (N + 1) + j] = G[j];
+        }
+        __syncwarp();
+        axis_pass(R, w, 0);
+        axis_pass(w, R, 1);
+        axis_pass(R, w, 2);
+        const T is = rsq(theta);
+        w[pa] *= ipow_t(is, oa);
+        if (two) w[pb] *= ipow_t(is, ob);
+        __syncwarp();
+        // a5: w -> R
+        if (model == 1) {
+            const T tau = fma(tauB[0], rho, tauA[0]) * ir;
+            const T om = rcp(tau);
+            const T bp = T(1) - (T(1) - es_b) * tau * rcp(fma(T(-0.5), es_b, tau));
+            const T sr = T(1) - om, s2 = fma(om, bp, sr), k4 = om * bp * bp * T(0.5) * ir;
+            auto es_slot = [&](int p, int n) {
+                T v = w[p];
+                if (n == 2) {
+                    v *= s2;
+                } else if (n == 4) {
+                    T t4 = T(0);
+                    for (int i = 0; i < tb.es_n[p]; ++i) t4 = fma(w[tb.es_q1[p][i]], w[tb.es_q2[p][i]], t4);
+                    v = fma(k4, t4, sr * v);
+                } else if (n >= 3) {
+                    v *= sr;
+                }
+                R[p] = v;
+            };
+            es_slot(pa, oa);
+            if (two) es_slot(pb, ob);
+        } else {
+            auto smrt_slot = [&](int p, int n) {
+                if (n < 2) {
+                    R[p] = w[p];
+                    return;
+                }
+                const int k0 = tau_slot(n, 0);  // s_m for m = 0, 1, 2 (n <= 5)
+                const T s0 = T(1) - rcp_tau<T>(tauA[k0], tauB[k0], rho);
+                const T s1 = T(1) - rcp_tau<T>(tauA[k0 + 1], tauB[k0 + 1], rho);
+                const T s2 = n >= 4 ? T(1) - rcp_tau<T>(tauA[k0 + 2], tauB[k0 + 2], rho) : T(0);
+                const int len = (n + 1) * (n + 2) / 2, o = ord_off(n), lp = p - o;
+                T acc = s0 * w[p];  // C_0 = s_0 B(n,0) D(n,0) = s_0
+                for (int j = 1; j <= n / 2; ++j) {
+                    T Cj = s0 * T(tb.bd[n][j][0]);
+                    Cj = fma(s1, T(tb.bd[n][j][1]), Cj);
+                    if (j >= 2) Cj = fma(s2, T(tb.bd[n][j][2]), Cj);
+                    const T *row = tb.rel + RelaxTables<N>::off(n, j) + lp * len;
+                    T dot = T(0);
+                    for (int q = 0; q < len; ++q) dot = fma(row[q], w[o + q], dot);
+                    acc = fma(Cj, dot, acc);
+                }
+                R[p] = acc;
+            };
+            smrt_slot(pa, oa);
+            if (two) smrt_slot(pb, ob);
+        }
+        // a6: theta^(|beta|/2), order 0 = rho, order 1 = 0, then T(u, theta)
+        const T sq = theta * is;
+        auto back_scale = [&](int p, int n) { R[p] = n == 0 ? rho : (n == 1 ? T(0) : R[p] * ipow_t(sq, n)); };
+        back_scale(pa, oa);
+        if (two) back_scale(pb, ob);
+        if (lane < 3) {
+            T G[N + 1];
+            maxwell_divided<N, T>(G, lane == 0 ? u0 : (lane == 1 ? u1 : u2), thm1);
+            for (int j = 0; j <= N; ++j) gs[lane * (N + 1) + j] = G[j];
+        }
+        __syncwarp();
+        axis_pass(R, w, 0);
+        axis_pass(w, R, 1);
+        axis_pass(R, w, 2);
+        if (lane == 0) w[0] = rhom1;  // deviation from the coefficients of w_i
+        __syncwarp();
+        // P_gamma = c^|gamma| sum_alpha hfull(alpha, gamma) ta_alpha (into R)
+        auto hf_row = [&](int p, int n) {
+            T acc = T(0);
+            for (int i = 0; i < tb.hf_n[p]; ++i) acc = fma(tb.hf_val[p][i], w[tb.hf_col[p][i]], acc);
+            R[p] = acc * ipow_t(c, n);
+        };
+        hf_row(pa, oa);
+        if (two) hf_row(pb, ob);
+        __syncwarp();
         return ok;
     }
 
@@ -803,8 +949,8 @@ __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a,
 // For problems too small to fill the GPU with one thread per cell (the paper's own runs are
 // single shocks of 100 cells), each block takes one cell: its d^3 pulled populations go to
 // shared memory, the x-rows and the raw moments are summed by the block's threads, the
-// moment-space steps run in warp 0 (every lane the same, lane 0 writes), and the rebuild is
-// spread over the x-rows again. Block b takes cell x0 + b % 32 of the 32-cell tile b / 32.
+// moment-space steps run in warp 0 with the coefficients spread over its lanes, and the
+// rebuild is spread over the x-rows again. Block b takes cell x0 + b % 32 of the 32-cell tile b / 32.
 template <class L1, int N, class T>
 struct TPCellShared {
     static constexpr int Q1 = L1::Q1, P2 = Q1 * Q1, Q = P2 * Q1, M = nmom(N);
@@ -812,6 +958,8 @@ struct TPCellShared {
     T g[P2][N + 1];     // x-row sums g_j of row (b, c) = b + d c
     T ep[Q1][N + 1];    // e_a^j
     T R[M];             // raw moments, then the rebuild coefficients
+    T w[M];             // moment-space scratch
+    T gs[3 * (N + 1)];  // per-axis Maxwellian coefficients of the frame transforms
 };
 
 template <class L1, int N, class T, bool FixedX>
@@ -821,7 +969,14 @@ __global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
     constexpr int Q1 = SH::Q1, P2 = SH::P2, Q = SH::Q, M = SH::M;
     __shared__ TPTables<L1, T> s;
     __shared__ SH sh;
-    tp_load_tables<L1>(a, s);
+    // double: the moment-space steps spread over warp 0's lanes need their tables in shared
+    // memory (a redundant full-warp FP64 instruction costs a full warp of the FP64 pipe); float
+    // keeps the one-thread form, whose compile-time constants beat the tables' latency
+    constexpr bool kLanes = std::is_same<T, double>::value;
+    struct NoTables {};
+    __shared__ typename std::conditional<kLanes, MomentSmem<N, double>, NoTables>::type ms;
+    if constexpr (kLanes) load_moment_smem<N>(ms);
+    tp_load_tables<L1>(a, s);  // ends with __syncthreads
     const int tid = threadIdx.x;
     const int2 tile = a.tiles[blockIdx.x >> 5];
     const InstanceInfo &in = a.inst[tile.x];
@@ -871,13 +1026,19 @@ __global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
     __syncthreads();
     // a2, a4-a6 in warp 0
     if (tid < 32) {
-        T R[M];
-        static_for<M>([&](auto G) { R[decltype(G)::value] = sh.R[decltype(G)::value]; });
-        const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in), in.model, T(in.es_b));
-        __syncwarp();
-        if (tid == 0) {
-            if (!ok) atomicOr(a.health, 1u);
-            static_for<M>([&](auto G) { sh.R[decltype(G)::value] = R[decltype(G)::value]; });
+        if constexpr (kLanes) {
+            const bool ok = C::collide_moments_lanes(ms, sh.R, sh.w, sh.gs, T(a.cd), tau_a<T>(in),
+                                                     tau_b<T>(in), in.model, T(in.es_b));
+            if (tid == 0 && !ok) atomicOr(a.health, 1u);
+        } else {
+            T R[M];
+            static_for<M>([&](auto G) { R[decltype(G)::value] = sh.R[decltype(G)::value]; });
+            const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in), in.model, T(in.es_b));
+            __syncwarp();
+            if (tid == 0) {
+                if (!ok) atomicOr(a.health, 1u);
+                static_for<M>([&](auto G) { sh.R[decltype(G)::value] = R[decltype(G)::value]; });
+            }
         }
     }
     __syncthreads();
