@@ -958,6 +958,7 @@ struct TPCellShared {
     T g[P2][N + 1];     // x-row sums g_j of row (b, c) = b + d c
     T ep[Q1][N + 1];    // e_a^j
     T R[M];             // raw moments, then the rebuild coefficients
+    T h[Q1][N + 1][N + 1];  // per z-plane c: sum over y of the x-row sums (then of the rebuild)
     T w[M];             // moment-space scratch
     T gs[3 * (N + 1)];  // per-axis Maxwellian coefficients of the frame transforms
 };
@@ -1012,15 +1013,21 @@ __global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
         static_for<N + 1>([&](auto J) { sh.g[row][decltype(J)::value] = g[decltype(J)::value]; });
     }
     __syncthreads();
-    // ... then y and z: R_(j,k,l) = sum_(b,c) g_(b,c)j e_b^k e_c^l, one moment per thread
+    // ... then y: h_c(j,k) = sum_b g_(b,c)j e_b^k ...
+    constexpr int JK = (N + 1) * (N + 1);
+    for (int q = tid; q < Q1 * JK; q += blockDim.x) {
+        const int c = q / JK, j = (q % JK) / (N + 1), k = q % (N + 1);
+        if (j + k > N) continue;
+        T acc = T(0);
+        for (int b = 0; b < Q1; ++b) acc = fma(sh.g[b + Q1 * c][j], sh.ep[b][k], acc);
+        sh.h[c][j][k] = acc;
+    }
+    __syncthreads();
+    // ... then z: R_(j,k,l) = sum_c h_c(j,k) e_c^l, one moment per thread
     for (int m = tid; m < M; m += blockDim.x) {
         const int j = mi_comp(m, 0), k = mi_comp(m, 1), l = mi_comp(m, 2);
         T acc = T(0);
-        for (int c = 0; c < Q1; ++c) {
-            T ac = T(0);
-            for (int b = 0; b < Q1; ++b) ac = fma(sh.g[b + Q1 * c][j], sh.ep[b][k], ac);
-            acc = fma(ac, sh.ep[c][l], acc);
-        }
+        for (int c = 0; c < Q1; ++c) acc = fma(sh.h[c][j][k], sh.ep[c][l], acc);
         sh.R[m] = acc;
     }
     __syncthreads();
@@ -1042,7 +1049,16 @@ __global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
         }
     }
     __syncthreads();
-    // a7 + a8: one x-row per thread, Pb_j = sum_(k,l) P_(j,k,l) e_b^k e_c^l
+    // a7 + a8: z first, Pc_c(j,k) = sum_l P_(j,k,l) e_c^l ...
+    for (int q = tid; q < Q1 * JK; q += blockDim.x) {
+        const int c = q / JK, j = (q % JK) / (N + 1), k = q % (N + 1);
+        if (j + k > N) continue;
+        T acc = T(0);
+        for (int l = 0; l + j + k <= N; ++l) acc = fma(sh.R[mi_pos(j, k, l)], sh.ep[c][l], acc);
+        sh.h[c][j][k] = acc;
+    }
+    __syncthreads();
+    // ... then one x-row per thread, Pb_j = sum_k Pc_c(j,k) e_b^k, stored as it is formed
     T *dst = a.fout + base + x;
     auto put = [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; };
     for (int row = tid; row < P2; row += blockDim.x) {
@@ -1053,12 +1069,7 @@ __global__ void __launch_bounds__(128) tp_step_cell_kernel(TPArgs<T> a) {
             T acc = T(0);
             static_for<N + 1 - j>([&](auto K) {
                 constexpr int k = decltype(K)::value;
-                T ac = T(0);
-                static_for<N + 1 - j - k>([&](auto Lm) {
-                    constexpr int l = decltype(Lm)::value;
-                    ac = fma(sh.R[mi_pos(j, k, l)], sh.ep[c][l], ac);
-                });
-                acc = fma(ac, sh.ep[b][k], acc);
+                acc = fma(sh.h[c][j][k], sh.ep[b][k], acc);
             });
             Pb[j] = acc;
         });
