@@ -169,7 +169,8 @@ lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 /* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128;
  * on D3Q729 and D3Q4913 each warp of the block takes its own 32-cell tile; on D3Q729 the value
  * 1 selects one block per cell -- its populations in shared memory, the factored sums spread
- * over the block -- which lb_init_lattice picks for problems of at most 12 cells per SM, and
+ * over the block -- which lb_init_lattice picks for problems of at most 48 (LB_F64) or 32 (LB_F32)
+ * cells per SM, and
  * which runs one launch per step only);
  * persistent = 1: lb_step runs all its steps in one cooperative launch of blocks_per_sm
  * blocks per SM (0 = as many as fit), tiles spread over the blocks, a grid-wide barrier between

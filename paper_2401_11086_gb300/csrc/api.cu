@@ -321,8 +321,9 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    // D3Q729 problems of at most 12 cells per SM take one block per cell (measured crossover)
-    if (e == cudaSuccess && c->kind == 2 && (long long)ncells <= 12LL * c->num_sms) {
+    // D3Q729 problems of at most 48 (double) or 32 (float) cells per SM take one block per cell
+    // (measured crossovers with the warp-staged kernel)
+    if (e == cudaSuccess && c->kind == 2 && (long long)ncells <= (prec == LB_F64 ? 48LL : 32LL) * c->num_sms) {
         c->sched.tile_width = 1;
         v.tile_width = 1;
     }
