@@ -380,6 +380,8 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     prec = args.precision
     ctx, f0, _ = shocks.setup_batch(d, 5, machs, lengths, precision=prec, width=0.0, theta1=theta1,
                                     stream=stream)
+    if args.es_b is not None:          # the ES-BGK model (Sec. 3) instead of SMRT
+        P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, args.es_b)
     sched = P.lb_get_schedule(ctx)   # the library's choice for this size
     fa, fb = f0, ctx.new_state()
     cur = P.lb_step(ctx, fa, fb, args.warmup)
@@ -438,12 +440,79 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     line = {"metric": METRIC, "value": rate / 1e9, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": f"table3_d3q729_n5_{prec}", "instances_per_gpu": len(machs),
+            "config": {"workload": f"table3_d3q729_n5_{prec}" + ("" if args.es_b is None else "_es_bgk"),
+                       "collision": "SMRT" if args.es_b is None else f"ES-BGK b={args.es_b}",
+                       "instances_per_gpu": len(machs),
                        "cells_per_gpu": cells, "velocities": q, "hermite_order": 5,
                        "state_bytes": elem * int(ctx.state_elems), "schedule": sched,
                        "l2": "L2 flushed (256 MB write) before every timed step" if small else
                              "inputs larger than L2"},
             "roofline": roof, "cpu_baseline": cpu, "gpu_launches": K, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_convergence(args, rank: int, local: int) -> None:
+    """The Appendix B study: smallest Hermite order of the 1D Maxwellian's expansion with L1
+    error below 0.01, on a 200 x 200 grid of theta in [0.1, 2] and u in [0, 4], orders <= 99."""
+    import numpy as np
+    import torch
+
+    import paper_2401_11086_gb300 as P
+
+    torch.cuda.set_device(local)
+    th = np.linspace(0.1, 2.0, 200)
+    uu = np.linspace(0.0, 4.0, 200)
+    T, U = np.meshgrid(th, uu, indexing="ij")
+    t = torch.from_numpy(T.ravel()).cuda()
+    u = torch.from_numpy(U.ravel()).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.lb_hermite_convergence(t, u)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        order, err = P.lb_hermite_convergence(t, u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    npts = t.numel()
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        code = f"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import convergence as CV
+pts = [(float(a), float(b)) for a in np.linspace(0.1, 2.0, 5) for b in np.linspace(0.0, 4.0, 4)]
+t0 = time.perf_counter()
+for th, u in pts:
+    CV.min_order(u, th)
+print(json.dumps({{"rate": len(pts) / (time.perf_counter() - t0)}}))
+"""
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        cpu = {"value": r["rate"], "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": "20 (theta, u) points of the same axes (5 x 4), orders <= 99, exact coefficients"}
+    if rank != 0:
+        return
+    o = order.cpu().numpy()
+    line = {"metric": "Appendix B convergence study throughput", "value": npts / (ms * 1e-3), "unit": "points/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hermite_convergence_200x200", "points": npts, "nmax": 99, "tol": 0.01,
+                       "quadrature": "Simpson, 4097 points", "orders_min_max": [int(o.min()), int(o.max())],
+                       "not_reached": int((o == 100).sum()),
+                       "l2": "inputs and outputs of a few hundred KB; the work is arithmetic"},
+            "roofline": {"bound": "alu", "note": "FP64 arithmetic on the recurrences and the Simpson sums",
+                         "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (fp64)", "frac": None,
+                         "traffic": None},
+            "cpu_baseline": cpu, "gpu_launches": args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -456,9 +525,12 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3"],
+    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence"],
                     help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
-                         "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5")
+                         "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5; convergence: the "
+                         "Appendix B study")
+    ap.add_argument("--es-b", type=float, default=None,
+                    help="table3 workload: run the ES-BGK model with this b instead of SMRT")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
                     help="table3 workload only")
     ap.add_argument("--instances", type=int, default=512, help="table3 workload: number of shocks")
@@ -476,6 +548,9 @@ def main():
         return
     if args.impl == "ours" and args.workload == "table3":
         run_table3(args, world, rank, local)
+        return
+    if args.impl == "ours" and args.workload == "convergence":
+        run_convergence(args, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, rank)
