@@ -50,7 +50,7 @@ typedef enum {
     LB_ERR_CUDA = 2,        /* a CUDA runtime call failed                                     */
     LB_ERR_UNSTABLE = 3,    /* a cell reached rho <= 0, theta <= 0 or NaN (health word)       */
     LB_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (health word)               */
-    LB_ERR_UNSUPPORTED = 5, /* valid request this build has no kernel for                     */
+    LB_ERR_UNSUPPORTED = 5, /* valid request the library has no kernel for                    */
     LB_ERR_NOMEM = 6        /* allocation of the context's own tables failed                  */
 } lb_status;
 

@@ -3,8 +3,8 @@
 Inputs are seeded and synthetic; every expected value comes from ``oracle/`` (or a golden file
 written by a script that calls only the oracle). Tolerances: FP64 kernels agree with the oracle
 to round-off (1e-11 relative to the population scale); FP32 kernels to 2e-6 per step relative
-to the population scale; FP32 runs of many steps are held to the benchmark spec's bound
-|delta rho| / rho <= 1e-5.
+to the population scale; FP32 runs of many steps are held to the mass-conservation
+bound |delta rho| / rho <= 1e-5.
 """
 import numpy as np
 import pytest
