@@ -75,9 +75,14 @@ struct StepArgs {
     unsigned step;            // step counter (stochastic rounding of the split precision)
 };
 
-// Stochastic rounding of a double to float: round to the float neighbour above or below with
-// probabilities proportional to the distances, drawn from a counter-based hash of
-// (cell, population, step), so that storing a steady state leaves no systematic bias.
+// Stochastic rounding of a double to float: the result is the float neighbour above or below
+// x with probabilities proportional to the closeness of x to each, drawn from a counter-based
+// hash of (cell, population, step), so that storing a steady state leaves no systematic bias.
+// On the bit pattern: a uniform 29-bit integer is added to the magnitude below the 24 bits a
+// float keeps (a carry rounds the magnitude up, with probability equal to the dropped fraction
+// of a float spacing; a carry into the exponent gives the next binade's first float), and the
+// dropped bits are cleared; the double left is a float, converted exactly. Infinities, NaNs
+// and magnitudes below the smallest normal float take the conversion toward zero instead.
 SMRT_D unsigned mix32(unsigned h) {  // the 32-bit finaliser of MurmurHash3
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -87,18 +92,35 @@ SMRT_D unsigned mix32(unsigned h) {  // the 32-bit finaliser of MurmurHash3
     return h;
 }
 SMRT_D float round_stochastic(double x, unsigned key) {
-    const float xf = __double2float_rn(x);
-    const double r = x - double(xf);
-    if (r == 0.0) return xf;
-    const float xn = nextafterf(xf, r > 0.0 ? INFINITY : -INFINITY);
-    const double gap = fabs(double(xn) - double(xf));
-    const double u = double(mix32(key) >> 8) * (1.0 / 16777216.0);
-    return (u * gap < fabs(r)) ? xn : xf;
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned long long sign = bits & 0x8000000000000000ull;
+    const unsigned long long mag = bits ^ sign;
+    const bool normal = mag >= 0x3810000000000000ull && mag < 0x7ff0000000000000ull;  // [2^-126, inf)
+    const unsigned long long r = static_cast<unsigned long long>(mix32(key) >> 3);      // 29 bits
+    const unsigned long long y = normal ? (((mag + r) & ~0x1fffffffull) | sign) : bits;
+    return __double2float_rz(__longlong_as_double(static_cast<long long>(y)));
 }
 
 template <class T>
 SMRT_D T rcp_tau(T A, T B, T rho) {
     return rho * rcp(fma(B, rho, A));
+}
+
+// Unnormalised Walsh-Hadamard transform of NB = 1, 2 or 4 values in place:
+// x_out[c] = sum_b (-1)^popcount(b & c) x_in[b].
+template <int NB, class U>
+SMRT_D void wht(U (&x)[NB]) {
+    static_for<(NB >= 4 ? 2 : (NB >= 2 ? 1 : 0))>([&](auto Tt) {
+        constexpr int bit = 1 << decltype(Tt)::value;
+        static_for<NB>([&](auto Bb) {
+            constexpr int b = decltype(Bb)::value;
+            if constexpr ((b & bit) == 0) {
+                const U lo = x[b], hi = x[b | bit];
+                x[b] = lo + hi;
+                x[b | bit] = lo - hi;
+            }
+        });
+    });
 }
 
 // ------------------------------------------------------------------------------ collision
@@ -108,6 +130,7 @@ struct Collide {
     static constexpr int NP = Lat::NP;
     static constexpr int M = nmom(N);
     static constexpr int KT = ntau(N);
+    static constexpr SignOrbits<Lat> kOrb = SignOrbits<Lat>();
 
     // a2: conserved sums, in Acc. The state holds deviations df_i = f_i - w_i; the quadrature
     // gives sum w_i = 1, sum w_i xi_i = 0, sum w_i |xi_i|^2 = 3, so
@@ -143,19 +166,57 @@ struct Collide {
         raw[2] = j1;
         raw[3] = j2;
         raw[4] = en;
-        rhom1 = r;
-        rho = Acc(1) + r;
+        from_raw_sums(raw, c, rho, rhom1, u, theta, thm1);
+    }
+    // rho, u, theta from the raw sums (sum df, sum e df, sum |e|^2 df)
+    SMRT_D static void from_raw_sums(const Acc (&raw)[5], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
+                                     Acc &theta, Acc &thm1) {
+        rhom1 = raw[0];
+        rho = Acc(1) + raw[0];
         const Acc ir = rcp(rho);
-        u[0] = c * j0 * ir;
-        u[1] = c * j1 * ir;
-        u[2] = c * j2 * ir;
+        u[0] = c * raw[1] * ir;
+        u[1] = c * raw[2] * ir;
+        u[2] = c * raw[3] * ir;
         const Acc uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        thm1 = (c * c * en - Acc(3) * r - rho * uu) * ir * Acc(1.0 / 3.0);
+        thm1 = (c * c * raw[4] - Acc(3) * raw[0] - rho * uu) * ir * Acc(1.0 / 3.0);
         theta = Acc(1) + thm1;
     }
 
-    // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma,
-    // R_gamma = sum_i f_i e_i^gamma, pairs folded: even |gamma| use f+ + f-, odd use f+ - f-.
+    // Raw moments R_gamma = sum_i f_i e_i^gamma, |gamma| <= Nm, summed per sign orbit: pair sums
+    // and differences, their Walsh-Hadamard transform over the orbit, then one multiply-add by
+    // the constant a^gamma per monomial that does not vanish on the orbit.
+    template <int Nm, class U>
+    SMRT_D static void raw_moments(const U (&f)[Q], U (&R)[nmom(Nm)]) {
+        constexpr int Mm = nmom(Nm);
+        static_for<Mm>([&](auto G) { R[decltype(G)::value] = U(0); });
+        R[0] = f[0];
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            U S[np], D[np];
+            static_for<np>([&](auto B) {
+                constexpr int b = decltype(B)::value, p = kOrb.pair[o][b];
+                constexpr bool fl = kOrb.flip[o][b] != 0;
+                S[b] = f[2 * p + 1] + f[2 * p + 2];
+                D[b] = fl ? f[2 * p + 2] - f[2 * p + 1] : f[2 * p + 1] - f[2 * p + 2];
+            });
+            wht<np>(S);
+            wht<np>(D);
+            static_for<Mm>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr int m = kOrb.monomial(o, g);
+                if constexpr (m != 0) {
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        R[g] = fma(U(m), S[cl], R[g]);
+                    else
+                        R[g] = fma(U(m), D[cl], R[g]);
+                }
+            });
+        });
+    }
+
+    // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma.
     template <int Nm>
     SMRT_D static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)]) {
         T Rc[nmom(Nm)];
@@ -164,40 +225,27 @@ struct Collide {
     // ... and the scaled raw moments Rc_gamma = c^|gamma| sum_i df_i e_i^gamma themselves
     template <int Nm>
     SMRT_D static void absolute(const T (&f)[Q], T c, T (&ta)[nmom(Nm)], T (&Rc)[nmom(Nm)]) {
+        raw_moments<Nm>(f, Rc);
+        scaled_to_absolute<Nm>(c, ta, Rc);
+    }
+    // Rc: raw moments in, scaled by c^|gamma| out; ta: the divided absolute coefficients
+    template <int Nm, class U>
+    SMRT_D static void scaled_to_absolute(U c, U (&ta)[nmom(Nm)], U (&Rc)[nmom(Nm)]) {
         constexpr int Mm = nmom(Nm);
-        T S[NP], D[NP];
-        static_for<NP>([&](auto P) {
-            constexpr int p = decltype(P)::value;
-            S[p] = f[2 * p + 1] + f[2 * p + 2];
-            D[p] = f[2 * p + 1] - f[2 * p + 2];
-        });
-        T cp[Nm + 1];
-        cp[0] = T(1);
+        U cp[Nm + 1];
+        cp[0] = U(1);
         static_for<Nm>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
         static_for<Mm>([&](auto G) {
             constexpr int g = decltype(G)::value;
-            constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-            constexpr bool even = ((g0 + g1 + g2) & 1) == 0;
-            T acc = (g == 0) ? f[0] : T(0);
-            static_for<NP>([&](auto P) {
-                constexpr int p = decltype(P)::value;
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
-                if constexpr (m != 0) {
-                    if constexpr (even)
-                        acc = fma(T(m), S[p], acc);
-                    else
-                        acc = fma(T(m), D[p], acc);
-                }
-            });
-            Rc[g] = acc * cp[g0 + g1 + g2];
+            if constexpr (mi_order(g) > 0) Rc[g] *= cp[mi_order(g)];
         });
         static_for<Mm>([&](auto A) {
             constexpr int al = decltype(A)::value;
-            T acc = T(0);
+            U acc = U(0);
             static_for<Mm>([&](auto G) {
                 constexpr int g = decltype(G)::value;
                 constexpr double h = hdiv(al, g);
-                if constexpr (h != 0.0) acc = fma(T(h), Rc[g], acc);
+                if constexpr (h != 0.0) acc = fma(U(h), Rc[g], acc);
             });
             ta[al] = acc;
         });
@@ -228,23 +276,37 @@ struct Collide {
             P[g] = acc * cp[mi_order(g)];
         });
         out[0] = U(wp[0]) * P[0];
-        static_for<NP>([&](auto Pp) {
-            constexpr int p = decltype(Pp)::value;
-            U ev = U(0), od = U(0);
+        // per sign orbit: sums of a^gamma P_gamma per parity class, their Walsh-Hadamard
+        // transform (the even and odd parts of the polynomial at each member), then the pair
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            U E[np], Od[np];
+            static_for<np>([&](auto B) {
+                E[decltype(B)::value] = U(0);
+                Od[decltype(B)::value] = U(0);
+            });
             static_for<M>([&](auto G) {
                 constexpr int g = decltype(G)::value;
-                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                constexpr int m = kOrb.monomial(o, g);
                 if constexpr (m != 0) {
-                    if constexpr (((g0 + g1 + g2) & 1) == 0)
-                        ev = fma(U(m), P[g], ev);
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        E[cl] = fma(U(m), P[g], E[cl]);
                     else
-                        od = fma(U(m), P[g], od);
+                        Od[cl] = fma(U(m), P[g], Od[cl]);
                 }
             });
-            const U w = U(wp[p + 1]);
-            out[2 * p + 1] = w * (ev + od);
-            out[2 * p + 2] = w * (ev - od);
+            wht<np>(E);
+            wht<np>(Od);
+            static_for<np>([&](auto B) {
+                constexpr int b = decltype(B)::value, p = kOrb.pair[o][b];
+                constexpr bool fl = kOrb.flip[o][b] != 0;
+                const U w = U(wp[p + 1]);
+                const U vplus = w * (E[b] + Od[b]), vminus = w * (E[b] - Od[b]);
+                out[2 * p + 1] = fl ? vminus : vplus;
+                out[2 * p + 2] = fl ? vplus : vminus;
+            });
         });
     }
 
@@ -270,10 +332,11 @@ struct Collide {
                                double cd, const T *tauA, const T *tauB, unsigned key = 0u,
                                const Acc *res = nullptr) {
         // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
-        T v[M], Rc[M];
-        absolute<N>(f, c, v, Rc);
+        T v[M];
         Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a, raw_a[5];
-        if constexpr (std::is_same<Acc, T>::value) {
+        if constexpr (!Split) {
+            T Rc[M];
+            absolute<N>(f, c, v, Rc);
             // a2 from the raw moments already formed: rho - 1 = Rc_0, rho u = Rc_1,
             // E - 3 = tr Rc_2
             rhom1_a = Rc[0];
@@ -287,22 +350,23 @@ struct Collide {
             thm1_a = (em3 - T(3) * rhom1_a - rho_a * uu) * ir * T(1.0 / 3.0);
             th_a = T(1) + thm1_a;
         } else {
-            conserved(f, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a, raw_a, res);
-        }
-        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
-        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
-        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
-        if constexpr (Split) {
-            // absolute coefficients in Acc, minus the Acc equilibrium: the float transforms
-            // below then act on the small non-equilibrium remainder only (d^eq = (rho, 0, ...)
-            // in the local frame, so d_n = [T^-1 (a - a^eq)]_n for n >= 2)
-            using CA = Collide<Lat, N, Acc, Acc, false>;
-            Acc fa[Q], va[M], Ra[M], teq[M];
+            // a2 and a3 in Acc from one set of raw moments, then the absolute coefficients
+            // minus the Acc equilibrium: the float transforms below act on the small
+            // non-equilibrium remainder only (d^eq = (rho, 0, ...) in the local frame, so
+            // d_n = [T^-1 (a - a^eq)]_n for n >= 2)
+            Acc fa[Q], Ra[M], va[M], teq[M];
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 fa[i] = res ? Acc(f[i]) + res[i] : Acc(f[i]);
             });
-            CA::template absolute<N>(fa, Acc(cd), va, Ra);
+            raw_moments<N>(fa, Ra);
+            raw_a[0] = Ra[0];
+            raw_a[1] = Ra[mi_pos(1, 0, 0)];
+            raw_a[2] = Ra[mi_pos(0, 1, 0)];
+            raw_a[3] = Ra[mi_pos(0, 0, 1)];
+            raw_a[4] = Ra[mi_pos(2, 0, 0)] + Ra[mi_pos(0, 2, 0)] + Ra[mi_pos(0, 0, 2)];
+            from_raw_sums(raw_a, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a);
+            scaled_to_absolute<N>(Acc(cd), va, Ra);
             equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
             teq[0] = rho_a;
             va[0] = rho_a;
@@ -310,9 +374,11 @@ struct Collide {
                 constexpr int p = decltype(A)::value;
                 v[p] = T(va[p] - teq[p]);
             });
-        } else {
-            v[0] = rho;
         }
+        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
+        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
+        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
+        if constexpr (!Split) v[0] = rho;
         to_local<N>(v, u, theta, thm1);
 
         // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u

@@ -130,4 +130,76 @@ struct D3Q103 {
     }
 };
 
+
+// Sign orbits. The sets above are closed under a change of sign of any component, so their
+// (+e, -e) pairs fall into orbits of vectors with the same absolute components a = |e|: an
+// orbit with k nonzero components holds 2^k vectors, i.e. 2^(k-1) pairs. Each member is
+// v = s (.) a with signs s; taking v = +e or -e of its pair so that v is positive on the first
+// nonzero axis ax[0], the member is labelled by the sign bits b of the other nonzero axes
+// (bit t-1 set when v is negative on ax[t]). Then v^gamma = a^gamma (-1)^popcount(b & pi),
+// pi = the parities of gamma on ax[1..k-1]: a monomial sum over the orbit is a^gamma times
+// one entry of a Walsh-Hadamard transform of the orbit's pair sums (even |gamma|) or pair
+// differences (odd |gamma|), and a rebuild is the same transform of per-parity-class sums.
+template <class Lat>
+struct SignOrbits {
+    static constexpr int NP = Lat::NP;
+    int n = 0;             // number of orbits
+    int k[NP] = {};        // nonzero components of the orbit's vectors
+    int ax[NP][3] = {};    // those axes, ascending
+    int a[NP][3] = {};     // absolute components
+    int pair[NP][4] = {};  // pair of the member with sign bits b
+    int flip[NP][4] = {};  // 1 when that member is -e of its pair
+    int seen[NP] = {};     // bit b set once the member with sign bits b is found
+    int count[NP] = {};
+    constexpr SignOrbits() {
+        for (int p = 0; p < NP; ++p) {
+            int m[3] = {0, 0, 0};
+            for (int d = 0; d < 3; ++d) m[d] = Lat::e(p, d) < 0 ? -Lat::e(p, d) : Lat::e(p, d);
+            int o = 0;
+            while (o < n && !(a[o][0] == m[0] && a[o][1] == m[1] && a[o][2] == m[2])) ++o;
+            if (o == n) {
+                for (int d = 0; d < 3; ++d) {
+                    a[o][d] = m[d];
+                    if (m[d] != 0) ax[o][k[o]++] = d;
+                }
+                ++n;
+            }
+            const int s0 = Lat::e(p, ax[o][0]) > 0 ? 1 : -1;
+            int b = 0;
+            for (int t = 1; t < k[o]; ++t)
+                if (s0 * Lat::e(p, ax[o][t]) < 0) b |= 1 << (t - 1);
+            pair[o][b] = p;
+            flip[o][b] = s0 < 0 ? 1 : 0;
+            seen[o] |= 1 << b;
+            ++count[o];
+        }
+    }
+    // every orbit holds each of its 2^(k-1) sign patterns exactly once (no rest vector here)
+    constexpr bool complete() const {
+        int pairs = 0;
+        for (int o = 0; o < n; ++o) {
+            const int np = 1 << (k[o] - 1);
+            if (k[o] < 1 || count[o] != np || seen[o] != (1 << np) - 1) return false;
+            pairs += np;
+        }
+        return pairs == NP;
+    }
+    // a^gamma for the multi-index in slot g (zero when gamma lies off the orbit's axes)
+    constexpr int monomial(int o, int g) const {
+        int v = 1;
+        for (int d = 0; d < 3; ++d)
+            for (int j = 0; j < mi_comp(g, d); ++j) v *= a[o][d];
+        return v;
+    }
+    // transform entry of slot g: the parities of gamma on ax[1..k-1]
+    constexpr int parity_class(int o, int g) const {
+        int c = 0;
+        for (int t = 1; t < k[o]; ++t)
+            if (mi_comp(g, ax[o][t]) & 1) c |= 1 << (t - 1);
+        return c;
+    }
+};
+static_assert(SignOrbits<D3Q39>().complete(), "D3Q39 is closed under sign changes");
+static_assert(SignOrbits<D3Q103>().complete(), "D3Q103 is closed under sign changes");
+
 }  // namespace smrt
