@@ -75,14 +75,33 @@ struct StepArgs {
     unsigned step;            // step counter (stochastic rounding of the split precision)
 };
 
+// Conversions between float and double on the IEEE 754 bit patterns, in integer instructions:
+// the split-precision step converts every population twice, and on this GPU the double
+// conversion instructions share the slow double-precision pipe with the arithmetic.
+// widen: binary32 -> binary64, exponent rebiased by 1023 - 127 = 896, fraction moved up 29 bits.
+// Zeros and subnormals (|x| < 2^-126) give signed zero; infinities and NaNs keep their class.
+template <class To, class From>
+SMRT_D To widen(From x) {
+    return To(x);
+}
+template <>
+SMRT_D double widen<double, float>(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned s = b & 0x80000000u, m = b ^ s;
+    unsigned hi = s | ((m >> 3) + (896u << 20)), lo = b << 29;
+    if (m < 0x00800000u) hi = s, lo = 0u;
+    if (m >= 0x7f800000u) hi = s | 0x7ff00000u | ((m >> 3) & 0x000fffffu);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
 // Stochastic rounding of a double to float: the result is the float neighbour above or below
 // x with probabilities proportional to the closeness of x to each, drawn from a counter-based
 // hash of (cell, population, step), so that storing a steady state leaves no systematic bias.
 // On the bit pattern: a uniform 29-bit integer is added to the magnitude below the 24 bits a
 // float keeps (a carry rounds the magnitude up, with probability equal to the dropped fraction
-// of a float spacing; a carry into the exponent gives the next binade's first float), and the
-// dropped bits are cleared; the double left is a float, converted exactly. Infinities, NaNs
-// and magnitudes below the smallest normal float take the conversion toward zero instead.
+// of a float spacing; a carry into the exponent gives the next binade's first float), the
+// dropped bits are discarded and the exponent rebiased. Magnitudes below 2^-126 give signed
+// zero, at or above 2^128 infinity; NaNs stay NaN.
 SMRT_D unsigned mix32(unsigned h) {  // the 32-bit finaliser of MurmurHash3
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -93,12 +112,14 @@ SMRT_D unsigned mix32(unsigned h) {  // the 32-bit finaliser of MurmurHash3
 }
 SMRT_D float round_stochastic(double x, unsigned key) {
     const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned long long sign = bits & 0x8000000000000000ull;
-    const unsigned long long mag = bits ^ sign;
-    const bool normal = mag >= 0x3810000000000000ull && mag < 0x7ff0000000000000ull;  // [2^-126, inf)
-    const unsigned long long r = static_cast<unsigned long long>(mix32(key) >> 3);      // 29 bits
-    const unsigned long long y = normal ? (((mag + r) & ~0x1fffffffull) | sign) : bits;
-    return __double2float_rz(__longlong_as_double(static_cast<long long>(y)));
+    const unsigned s = static_cast<unsigned>(bits >> 32) & 0x80000000u;
+    const unsigned long long mag = bits & 0x7fffffffffffffffull;
+    const unsigned long long t = mag + static_cast<unsigned long long>(mix32(key) >> 3);  // 29 bits
+    unsigned y = s | (static_cast<unsigned>(t >> 29) - (896u << 23));
+    if (mag < 0x3810000000000000ull) y = s;                               // below 2^-126
+    if (t >= 0x47f0000000000000ull) y = s | 0x7f800000u;                  // 2^128 and above
+    if (mag > 0x7ff0000000000000ull) y = s | 0x7fc00000u;                 // NaN
+    return __uint_as_float(y);
 }
 
 template <class T>
@@ -144,17 +165,20 @@ struct Collide {
     }
     // ... also returning the raw sums (sum df, sum e df, sum |e|^2 df) in raw[0..4]
     SMRT_D static void conserved(const T (&f)[Q], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
-                                 Acc &theta, Acc &thm1, Acc (&raw)[5], const Acc *res = nullptr) {
-        // res (optional): what the stored float values lack against their exact values
-        // (end-state populations pulled from beyond a fixed end, kept in double)
-        auto val = [&](int i) { return res ? Acc(f[i]) + res[i] : Acc(f[i]); };
-        Acc r = val(0), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
+                                 Acc &theta, Acc &thm1, Acc (&raw)[5]) {
+        conserved_sums(f, raw);
+        from_raw_sums(raw, c, rho, rhom1, u, theta, thm1);
+    }
+    // sum x_i, sum e_i x_i, sum |e_i|^2 x_i in Acc, pairs folded
+    template <class U>
+    SMRT_D static void conserved_sums(const U (&x)[Q], Acc (&raw)[5]) {
+        Acc r = widen<Acc>(x[0]), j0 = Acc(0), j1 = Acc(0), j2 = Acc(0), en = Acc(0);
         static_for<NP>([&](auto P) {
             constexpr int p = decltype(P)::value;
             constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
             constexpr int ee = e0 * e0 + e1 * e1 + e2 * e2;
-            const Acc sp = val(2 * p + 1) + val(2 * p + 2);
-            const Acc dp = val(2 * p + 1) - val(2 * p + 2);
+            const Acc xp = widen<Acc>(x[2 * p + 1]), xm = widen<Acc>(x[2 * p + 2]);
+            const Acc sp = xp + xm, dp = xp - xm;
             r += sp;
             if constexpr (e0 != 0) j0 = fma(Acc(e0), dp, j0);
             if constexpr (e1 != 0) j1 = fma(Acc(e1), dp, j1);
@@ -166,7 +190,6 @@ struct Collide {
         raw[2] = j1;
         raw[3] = j2;
         raw[4] = en;
-        from_raw_sums(raw, c, rho, rhom1, u, theta, thm1);
     }
     // rho, u, theta from the raw sums (sum df, sum e df, sum |e|^2 df)
     SMRT_D static void from_raw_sums(const Acc (&raw)[5], Acc c, Acc &rho, Acc &rhom1, Acc (&u)[3],
@@ -259,8 +282,17 @@ struct Collide {
 
     // a7 + a8 helper: values f'_i = w_i sum_gamma P_gamma e_i^gamma with
     // P_gamma = c^|gamma| sum_alpha hfull(alpha, gamma) ta'_alpha; U is the arithmetic type.
+    // corr (optional): (base, B_0, B_1, B_2, C) added to the monomial coefficients P of orders
+    // 0, 1 and the diagonal of 2, i.e. w_i (base + B.e_i + C |e_i|^2) added to every out_i.
     template <class U, class W>
-    SMRT_D static void rebuild(const U (&ta)[M], U c, const W (&wp)[NP + 1], U (&out)[Q]) {
+    SMRT_D static void rebuild(const U (&ta)[M], U c, const W (&wp)[NP + 1], U (&out)[Q],
+                               const U *corr = nullptr) {
+        rebuild_emit(ta, c, wp, [&](int i, U v) { out[i] = v; }, corr);
+    }
+    // ... handing each value to put(i, value) as soon as it is formed
+    template <class U, class W, class Put>
+    SMRT_D static void rebuild_emit(const U (&ta)[M], U c, const W (&wp)[NP + 1], Put &&put,
+                                    const U *corr = nullptr) {
         U cp[N + 1];
         cp[0] = U(1);
         static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * c; });
@@ -275,7 +307,16 @@ struct Collide {
             });
             P[g] = acc * cp[mi_order(g)];
         });
-        out[0] = U(wp[0]) * P[0];
+        if (corr) {
+            P[0] += corr[0];
+            P[mi_pos(1, 0, 0)] += corr[1];
+            P[mi_pos(0, 1, 0)] += corr[2];
+            P[mi_pos(0, 0, 1)] += corr[3];
+            P[mi_pos(2, 0, 0)] += corr[4];
+            P[mi_pos(0, 2, 0)] += corr[4];
+            P[mi_pos(0, 0, 2)] += corr[4];
+        }
+        put(0, U(wp[0]) * P[0]);
         // per sign orbit: sums of a^gamma P_gamma per parity class, their Walsh-Hadamard
         // transform (the even and odd parts of the polynomial at each member), then the pair
         static_for<kOrb.n>([&](auto O) {
@@ -304,8 +345,8 @@ struct Collide {
                 constexpr bool fl = kOrb.flip[o][b] != 0;
                 const U w = U(wp[p + 1]);
                 const U vplus = w * (E[b] + Od[b]), vminus = w * (E[b] - Od[b]);
-                out[2 * p + 1] = fl ? vminus : vplus;
-                out[2 * p + 2] = fl ? vplus : vminus;
+                put(2 * p + 1, fl ? vminus : vplus);
+                put(2 * p + 2, fl ? vplus : vminus);
             });
         });
     }
@@ -326,61 +367,12 @@ struct Collide {
         ta[0] = rhom1;
     }
 
-    // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
-    // Returns false when rho or theta is not positive (or NaN).
-    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const double (&wpd)[NP + 1], T c,
-                               double cd, const T *tauA, const T *tauB, unsigned key = 0u,
-                               const Acc *res = nullptr) {
-        // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
-        T v[M];
-        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a, raw_a[5];
-        if constexpr (!Split) {
-            T Rc[M];
-            absolute<N>(f, c, v, Rc);
-            // a2 from the raw moments already formed: rho - 1 = Rc_0, rho u = Rc_1,
-            // E - 3 = tr Rc_2
-            rhom1_a = Rc[0];
-            rho_a = T(1) + rhom1_a;
-            const T ir = rcp(rho_a);
-            u_a[0] = Rc[mi_pos(1, 0, 0)] * ir;
-            u_a[1] = Rc[mi_pos(0, 1, 0)] * ir;
-            u_a[2] = Rc[mi_pos(0, 0, 1)] * ir;
-            const T uu = u_a[0] * u_a[0] + u_a[1] * u_a[1] + u_a[2] * u_a[2];
-            const T em3 = Rc[mi_pos(2, 0, 0)] + Rc[mi_pos(0, 2, 0)] + Rc[mi_pos(0, 0, 2)];
-            thm1_a = (em3 - T(3) * rhom1_a - rho_a * uu) * ir * T(1.0 / 3.0);
-            th_a = T(1) + thm1_a;
-        } else {
-            // a2 and a3 in Acc from one set of raw moments, then the absolute coefficients
-            // minus the Acc equilibrium: the float transforms below act on the small
-            // non-equilibrium remainder only (d^eq = (rho, 0, ...) in the local frame, so
-            // d_n = [T^-1 (a - a^eq)]_n for n >= 2)
-            Acc fa[Q], Ra[M], va[M], teq[M];
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                fa[i] = res ? Acc(f[i]) + res[i] : Acc(f[i]);
-            });
-            raw_moments<N>(fa, Ra);
-            raw_a[0] = Ra[0];
-            raw_a[1] = Ra[mi_pos(1, 0, 0)];
-            raw_a[2] = Ra[mi_pos(0, 1, 0)];
-            raw_a[3] = Ra[mi_pos(0, 0, 1)];
-            raw_a[4] = Ra[mi_pos(2, 0, 0)] + Ra[mi_pos(0, 2, 0)] + Ra[mi_pos(0, 0, 2)];
-            from_raw_sums(raw_a, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a);
-            scaled_to_absolute<N>(Acc(cd), va, Ra);
-            equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
-            teq[0] = rho_a;
-            va[0] = rho_a;
-            static_for<M>([&](auto A) {
-                constexpr int p = decltype(A)::value;
-                v[p] = T(va[p] - teq[p]);
-            });
-        }
-        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
-        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
-        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
-        if constexpr (!Split) v[0] = rho;
+    // a4-a6 on divided absolute coefficients v: to the local frame, relaxation of orders 2..N
+    // with their own times, back to the absolute frame (truncated at N); the slot of order 0
+    // leaves as o0 and those of order 1 as zero (u is the frame velocity).
+    SMRT_D static void relax_coefficients(T (&v)[M], const T (&u)[3], T rho, T theta, T thm1, T o0,
+                                          const T *tauA, const T *tauB) {
         to_local<N>(v, u, theta, thm1);
-
         // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u
         T s[KT];
         static_for<KT>([&](auto K) {
@@ -388,7 +380,6 @@ struct Collide {
             s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
         });
         static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
-
         // a6: back to the absolute frame: scale by theta^(|beta|/2), transform with T(u, theta)
         const T sq = theta * rsq(theta);
         T sp[N + 1];
@@ -397,7 +388,7 @@ struct Collide {
         static_for<M>([&](auto A) {
             constexpr int p = decltype(A)::value;
             if constexpr (mi_order(p) == 0)
-                v[p] = Split ? T(0) : rho;
+                v[p] = o0;
             else if constexpr (mi_order(p) == 1)
                 v[p] = T(0);
             else
@@ -409,58 +400,89 @@ struct Collide {
             maxwell_divided<N, T>(G[k], u[k], thm1);
         });
         binomial_divided<N, T>(v, G);
+    }
 
-        if constexpr (!Split) {
-            v[0] = T(rhom1_a);  // deviation from the coefficients of w_i
+    // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
+    // Returns false when rho or theta is not positive (or NaN).
+    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const double (&wpd)[NP + 1], T c,
+                               double cd, const T *tauA, const T *tauB, unsigned key = 0u) {
+        if constexpr (Split) {
+            Acc fa[Q];
+            static_for<Q>([&](auto I) { fa[decltype(I)::value] = widen<Acc>(f[decltype(I)::value]); });
+            return collide_split(fa, f, wp, wpd, c, cd, tauA, tauB, key);
+        } else {
+            // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
+            T v[M], Rc[M];
+            absolute<N>(f, c, v, Rc);
+            // a2 from the raw moments already formed: rho - 1 = Rc_0, rho u = Rc_1,
+            // E - 3 = tr Rc_2
+            const T rhom1 = Rc[0];
+            const T rho = T(1) + rhom1;
+            const T ir = rcp(rho);
+            const T u[3] = {Rc[mi_pos(1, 0, 0)] * ir, Rc[mi_pos(0, 1, 0)] * ir, Rc[mi_pos(0, 0, 1)] * ir};
+            const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const T em3 = Rc[mi_pos(2, 0, 0)] + Rc[mi_pos(0, 2, 0)] + Rc[mi_pos(0, 0, 2)];
+            const T thm1 = (em3 - T(3) * rhom1 - rho * uu) * ir * T(1.0 / 3.0);
+            const T theta = T(1) + thm1;
+            const bool ok = (rho > T(0)) && (theta > T(0));
+            v[0] = rho;
+            relax_coefficients(v, u, rho, theta, thm1, rho, tauA, tauB);
+            v[0] = rhom1;  // deviation from the coefficients of w_i
             T out[Q];
             rebuild<T>(v, c, wp, out);
             static_for<Q>([&](auto I) { f[decltype(I)::value] = out[decltype(I)::value]; });
-        } else {
-            // equilibrium part in Acc from the Acc moments, non-equilibrium part in T
-            Acc teq[M];
-            equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
-            // the equilibrium part takes the weights in double: float-rounded weights would
-            // bias the conserved moments of every cell by ~1e-8 per step
-            Acc out[Q];
-            rebuild<Acc>(teq, Acc(cd), wpd, out);
-            T oneq[Q];
-            rebuild<T>(v, c, wp, oneq);
-            static_for<Q>([&](auto I) { out[decltype(I)::value] += Acc(oneq[decltype(I)::value]); });
-            // Conservation in Acc: float arithmetic in the non-equilibrium part leaves errors
-            // that freeze once the flow is steady and would drift rho, rho u and E. Restore the
-            // pre-collision sums exactly along the conserved directions
-            //   d_i = w_i (A + B.e_i + C (|e_i|^2 - 3/c^2)),
-            // using sum w = 1, sum w e e = 1/c^2, sum w |e|^2 = 3/c^2, sum w |e|^4 = 15/c^4.
-            Acc m0 = out[0], m1 = Acc(0), m2 = Acc(0), m3 = Acc(0), m4 = Acc(0);
-            static_for<NP>([&](auto P) {
-                constexpr int p = decltype(P)::value;
-                constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
-                const Acc sp = out[2 * p + 1] + out[2 * p + 2], dp = out[2 * p + 1] - out[2 * p + 2];
-                m0 += sp;
-                if constexpr (e0 != 0) m1 = fma(Acc(e0), dp, m1);
-                if constexpr (e1 != 0) m2 = fma(Acc(e1), dp, m2);
-                if constexpr (e2 != 0) m3 = fma(Acc(e2), dp, m3);
-                m4 = fma(Acc(e0 * e0 + e1 * e1 + e2 * e2), sp, m4);
-            });
-            const Acc c2 = Acc(cd) * Acc(cd);
-            const Acc A = raw_a[0] - m0;
-            const Acc B0 = c2 * (raw_a[1] - m1), B1 = c2 * (raw_a[2] - m2), B2 = c2 * (raw_a[3] - m3);
-            const Acc C = c2 * c2 * (raw_a[4] - m4 - Acc(3) * A / c2) / Acc(6);
-            const Acc base = A - C * Acc(3) / c2;
-            out[0] += Acc(wpd[0]) * base;
-            static_for<NP>([&](auto P) {
-                constexpr int p = decltype(P)::value;
-                constexpr int e0 = Lat::e(p, 0), e1 = Lat::e(p, 1), e2 = Lat::e(p, 2);
-                const Acc ev = base + C * Acc(e0 * e0 + e1 * e1 + e2 * e2);
-                const Acc od = B0 * Acc(e0) + B1 * Acc(e1) + B2 * Acc(e2);
-                out[2 * p + 1] += Acc(wpd[p + 1]) * (ev + od);
-                out[2 * p + 2] += Acc(wpd[p + 1]) * (ev - od);
-            });
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                f[i] = round_stochastic(out[i], key ^ (0x9e3779b9u * (i + 1)));
-            });
+            return ok;
         }
+    }
+
+    // Split precision (T float, Acc double): fa = the pulled populations in Acc (exact end-state
+    // values at ghost slots), f = the post-collision populations, rounded stochastically to T.
+    // In Acc: the raw moments, the conserved moments, the absolute coefficients and the
+    // equilibrium they are reduced by, and the rebuild of the equilibrium with the weights and c
+    // in Acc; in T: the non-equilibrium remainder through a4-a6 and its rebuild.
+    SMRT_D static bool collide_split(const Acc (&fa)[Q], T (&f)[Q], const T (&wp)[NP + 1],
+                                     const double (&wpd)[NP + 1], T c, double cd, const T *tauA,
+                                     const T *tauB, unsigned key) {
+        Acc Ra[M], va[M], teq[M], raw[5];
+        raw_moments<N>(fa, Ra);
+        raw[0] = Ra[0];
+        raw[1] = Ra[mi_pos(1, 0, 0)];
+        raw[2] = Ra[mi_pos(0, 1, 0)];
+        raw[3] = Ra[mi_pos(0, 0, 1)];
+        raw[4] = Ra[mi_pos(2, 0, 0)] + Ra[mi_pos(0, 2, 0)] + Ra[mi_pos(0, 0, 2)];
+        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a;
+        from_raw_sums(raw, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a);
+        scaled_to_absolute<N>(Acc(cd), va, Ra);
+        equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
+        // the non-equilibrium remainder a - a^eq (d^eq = (rho, 0, ...) in the local frame, so
+        // d_n = [T^-1 (a - a^eq)]_n for n >= 2); slot 0 carries nothing of it
+        T v[M];
+        v[0] = T(0);
+        static_for<M - 1>([&](auto A) {
+            constexpr int p = decltype(A)::value + 1;
+            v[p] = T(va[p] - teq[p]);
+        });
+        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
+        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
+        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
+        relax_coefficients(v, u, rho, theta, thm1, T(0), tauA, tauB);
+        T oneq[Q];
+        rebuild<T>(v, c, wp, oneq);
+        // Conservation in Acc. The equilibrium rebuilt in Acc carries the pre-collision rho, rho u
+        // and E (the quadrature is exact for them), while the float remainder, zero in those
+        // moments in exact arithmetic, carries rounding errors that freeze once the flow is
+        // steady and would drift them. Its sums, exact in Acc, are removed along the conserved
+        // directions d_i = w_i (A + B.e_i + C (|e_i|^2 - 3/c^2)) (sum w = 1, sum w e e = 1/c^2,
+        // sum w |e|^2 = 3/c^2, sum w |e|^4 = 15/c^4), folded into the equilibrium's coefficients.
+        Acc m[5];
+        conserved_sums(oneq, m);
+        const Acc c2 = Acc(cd) * Acc(cd);
+        const Acc A = -m[0];
+        const Acc C = c2 * c2 * (-m[4] - Acc(3) * A / c2) / Acc(6);
+        const Acc corr[5] = {A - C * Acc(3) / c2, -c2 * m[1], -c2 * m[2], -c2 * m[3], C};
+        rebuild_emit(teq, Acc(cd), wpd, [&](int i, Acc v) {
+            f[i] = round_stochastic(v + widen<Acc>(oneq[i]), key ^ (0x9e3779b9u * unsigned(i + 1)));
+        }, corr);
         return ok;
     }
 };
@@ -526,49 +548,39 @@ SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *_
     const T *gr = gl + Lat::Q;
     const double *gld = a.ghostsd + (long long)tile.x * 2 * Lat::Q;
     const double *grd = gld + Lat::Q;
-    constexpr bool Res = Split && FixedX;  // keep the float end states' rounding residuals
-    Acc res[Lat::Q];
-    if constexpr (Res) static_for<Lat::Q>([&](auto I) { res[decltype(I)::value] = Acc(0); });
-    T f[Lat::Q];
-    {  // the rest population streams by k as well
-        const int xs = x - in.kx;
+    // pull of population i from cell xs of the instance: the stored state inside, the end
+    // states beyond a fixed end (in double for the split precision, exact)
+    using V = typename std::conditional<Split, Acc, T>::type;
+    auto pull = [&](int i, int xs) -> V {
         if constexpr (FixedX) {
-            if (xs < 0) {
-                f[0] = gl[0];
-                if constexpr (Res) res[0] = Acc(gld[0]) - Acc(gl[0]);
-            } else if (xs >= L) {
-                f[0] = gr[0];
-                if constexpr (Res) res[0] = Acc(grd[0]) - Acc(gr[0]);
+            if constexpr (Split) {
+                if (xs < 0) return V(gld[i]);
+                if (xs >= L) return V(grd[i]);
             } else {
-                f[0] = load_pop<Coherent>(fin + a.plane[0] + base + xs);
+                if (xs < 0) return gl[i];
+                if (xs >= L) return gr[i];
             }
+            return widen<V>(load_pop<Coherent>(fin + a.plane[i] + base + xs));
         } else {
-            f[0] = load_pop<Coherent>(fin + a.plane[0] + base + wrap(xs, L));
+            return widen<V>(load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L)));
         }
-    }
+    };
+    V fv[Lat::Q];
+    fv[0] = pull(0, x - in.kx);  // the rest population streams by k as well
     static_for<Lat::NP>([&](auto P) {
         constexpr int p = decltype(P)::value;
-        static_for<2>([&](auto Sg) {
-            constexpr int sg = decltype(Sg)::value == 0 ? 1 : -1;
-            constexpr int i = 2 * p + 1 + decltype(Sg)::value;
-            const int xs = x - (sg * Lat::e(p, 0) + in.kx);
-            if constexpr (FixedX) {
-                if (xs < 0) {
-                    f[i] = gl[i];
-                    if constexpr (Res) res[i] = Acc(gld[i]) - Acc(gl[i]);
-                } else if (xs >= L) {
-                    f[i] = gr[i];
-                    if constexpr (Res) res[i] = Acc(grd[i]) - Acc(gr[i]);
-                } else {
-                    f[i] = load_pop<Coherent>(fin + a.plane[i] + base + xs);
-                }
-            } else {
-                f[i] = load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L));
-            }
-        });
+        fv[2 * p + 1] = pull(2 * p + 1, x - (Lat::e(p, 0) + in.kx));
+        fv[2 * p + 2] = pull(2 * p + 2, x - (-Lat::e(p, 0) + in.kx));
     });
-    const bool ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
-                               mix32(unsigned(base + x) ^ mix32(step)), Res ? res : nullptr);
+    T f[Lat::Q];
+    bool ok;
+    if constexpr (Split)
+        ok = C::collide_split(fv, f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
+                              mix32(unsigned(base + x) ^ mix32(step)));
+    else
+        ok = C::collide(fv, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
+                        mix32(unsigned(base + x) ^ mix32(step)));
+    if constexpr (!Split) static_for<Lat::Q>([&](auto I) { f[decltype(I)::value] = fv[decltype(I)::value]; });
     if (!ok) atomicOr(a.health, 1u);
     static_for<Lat::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
