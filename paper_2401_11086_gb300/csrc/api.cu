@@ -292,6 +292,9 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         for (int p = 0; p < c->np; ++p) v.wp[p + 1] = lat->w[c->perm[2 * p + 1]];
     }
     for (int k = 0; k < kMaxQ1; ++k) v.w1[k] = w1[k];
+    v.plane_identity = 1;
+    for (int i = 0; i < c->q; ++i)
+        if (c->perm[i] != i) v.plane_identity = 0;
     v.stride = (long long)c->stride;
     v.c = lat->c;
     v.nx = line ? c->nx_inst[0] : grid->nx;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstring>
 
 #include "kernels.cuh"
 #include "tensor.cuh"
@@ -41,6 +42,7 @@ struct CtxView {
     const int *plane_idx;
     long long stride;
     double w1[kMaxQ1];
+    int plane_identity;  // 1: library population i is caller plane i (tensor-map staging applies)
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
@@ -207,7 +209,48 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
     for (int k = 0; k < kMaxQ1; ++k) a.w1[k] = v.w1[k];
     a.cd = v.c;
     a.step = v.step;
+    a.tma = 0;
     return a;
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link-time dependence on the
+// driver library).
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+inline TensorMapEncodeFn tensor_map_encoder() {
+    static const TensorMapEncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return TensorMapEncodeFn(nullptr);
+        return reinterpret_cast<TensorMapEncodeFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a state for the warp-staged kernels: [Q planes][stride elements], box of
+// kSeg x d (one x-row group). False when the staging cannot use it (caller order differs from
+// the library order, a plane stride or base address not on 16 bytes, coordinates beyond int32)
+// or the driver refuses it; the kernels then copy plane by plane.
+template <class L1, class T>
+bool tp_encode_map(const CtxView &v, const void *state, CUtensorMap *m) {
+    constexpr int Q = L1::Q1 * L1::Q1 * L1::Q1;
+    const TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc || !v.plane_identity || !state) return false;
+    if ((reinterpret_cast<unsigned long long>(state) & 15ull) != 0ull || (v.stride * (long long)sizeof(T)) % 16 != 0 ||
+        v.stride + 2 * TPWarpStage<L1, T>::kSeg >= (1ll << 31))
+        return false;
+    const cuuint64_t dims[2] = {cuuint64_t(v.stride), cuuint64_t(Q)};
+    const cuuint64_t strides[1] = {cuuint64_t(v.stride) * sizeof(T)};
+    const cuuint32_t box[2] = {cuuint32_t(TPWarpStage<L1, T>::kSeg), cuuint32_t(L1::Q1)};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+               const_cast<void *>(state), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // The warp-staged kernels may take more than the default 48 KB of dynamic shared memory:
@@ -237,7 +280,7 @@ inline int tp_blocks(const CtxView &v) {
 
 template <class L1, int N, class T>
 cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
-    const TPArgs<T> a = make_tp_args<T>(v, fin, fout);
+    TPArgs<T> a = make_tp_args<T>(v, fin, fout);
     if (v.tile_width == 1) {  // one cell per block (D1Q9-P1 sets only: its tables fit in 48 KB)
         if constexpr (L1::Q1 == 9) {
             if (v.fixedx)
@@ -250,14 +293,17 @@ cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
         }
     }
     const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
+    TPMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    a.tma = tp_encode_map<L1, T>(v, fin, &maps.src) ? 1 : 0;
     if (v.fixedx) {
         const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true>, L1, T>();
         if (e != cudaSuccess) return e;
-        tp_step_line_warp<L1, N, T, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles);
+        tp_step_line_warp<L1, N, T, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
     } else {
         const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, false>, L1, T>();
         if (e != cudaSuccess) return e;
-        tp_step_line_warp<L1, N, T, false><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles);
+        tp_step_line_warp<L1, N, T, false><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
     }
     return cudaGetLastError();
 }
@@ -286,7 +332,10 @@ cudaError_t tp_launch_ghost(const CtxView &v, const double *states, int ninst, v
 
 template <class L1, int N, class T>
 cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, int grid) {
-    const TPArgs<T> a = make_tp_args<T>(v, fa, fb);
+    TPArgs<T> a = make_tp_args<T>(v, fa, fb);
+    TPMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    a.tma = (tp_encode_map<L1, T>(v, fa, &maps.src) && tp_encode_map<L1, T>(v, fb, &maps.dst)) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(v.tile_width);
@@ -302,11 +351,11 @@ cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nstep
     if (v.fixedx) {
         const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
         if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true>, a, nsteps, ntiles, bar);
+        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true>, a, nsteps, ntiles, bar, maps);
     }
     const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, false>, L1, T>();
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, false>, a, nsteps, ntiles, bar);
+    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, false>, a, nsteps, ntiles, bar, maps);
 }
 
 template <class L1, int N, class T>

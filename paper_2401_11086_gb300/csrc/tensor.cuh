@@ -20,6 +20,8 @@
 // Ghost populations (end states beyond a fixed x end) are kept in library order.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded by the host)
+
 #include "kernels.cuh"
 #include "moment_tables.cuh"
 
@@ -64,6 +66,14 @@ struct TPArgs {
     double w1[kMaxQ1];                 // 1D weights, library order
     double cd;                         // lattice scale c
     unsigned step;
+    int tma;                           // 1: the kernel's tensor maps describe fin and fout
+};
+
+// Tensor maps of the two states for the warp-staged kernels: a 2D view [plane][stride] of a
+// state (library order = caller order), box of kSeg elements x d planes (one x-row group).
+struct TPMaps {
+    CUtensorMap src;  // of TPArgs::fin
+    CUtensorMap dst;  // of TPArgs::fout
 };
 
 // Shared-memory tables of one block: caller planes, the 1D abscissae (integers, as T) and the
@@ -673,6 +683,16 @@ SMRT_D void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned l
                  "l"(src), "r"(bytes), "r"(smem_addr(b))
                  : "memory");
 }
+// One box of a 2D tensor map (coordinates: element within the plane, plane) -> shared memory,
+// bytes counted against mbarrier b. The x coordinate must be a multiple of 16 bytes; the
+// destination is 128-byte aligned. Elements outside the tensor read as zero.
+SMRT_D void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_addr(b))
+        : "memory");
+}
 // Order this thread's earlier generic-proxy accesses of shared (global) memory before its
 // later async-proxy ones: a buffer read or written by the threads, then refilled by the copy
 // engine; data written by other blocks, then copied.
@@ -719,10 +739,14 @@ struct TPWarpStage {
     static constexpr int kEmax = L1::E(L1::NP1 - 1);    // largest |e| of the 1D rule
     static constexpr int kSeg = kW + ((2 * kEmax + kAlign - 1) + kAlign - 1) / kAlign * kAlign;
     static constexpr int kRows = 2 * L1::Q1;            // planes of the largest stage
+    // a stage buffer holds two groups of d rows (the +e_b and -e_b x-rows), each group
+    // starting 128-byte aligned so that one tensor-map box fills it
+    static constexpr int kGrp = int((L1::Q1 * kSeg * sizeof(T) + 127) / 128 * 128 / sizeof(T));
+    static constexpr int kStage = 2 * kGrp;             // elements per stage buffer
     static constexpr int kPerZ = L1::NP1 + 1;           // stages per z-plane
     static constexpr int kTotal = L1::Q1 * kPerZ;       // stages per step
     static constexpr size_t kWarpBytes =                // mbarriers, then the stage buffers
-        (128 + size_t(kStages) * kRows * kSeg * sizeof(T) + 127) / 128 * 128;
+        128 + size_t(kStages) * kStage * sizeof(T);
     SMRT_HD static size_t bytes(int threads) { return size_t(threads / 32) * kWarpBytes; }
 };
 
@@ -730,10 +754,11 @@ struct TPWarpStage {
 // is the parity of buffer b's next fill, bit b of pending says that fill is in flight. All 32
 // lanes call it (lanes past the line's end idle). Returns false, with LB_HEALTH_TIMEOUT in
 // the health word, when a fill did not land within the bounded wait.
+// tm: tensor map of fin (one box per x-row group), or null to copy plane by plane.
 template <class L1, int N, class T, bool FixedX, bool Coherent>
 SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *__restrict__ fin,
                          T *__restrict__ fout, int tile_index, T *buf, unsigned long long *bar, unsigned &parity,
-                         unsigned &pending) {
+                         unsigned &pending, const CUtensorMap *tm) {
     using C = TPCell<L1, N, T>;
     using S = TPWarpStage<L1, T>;
     constexpr int Q1 = L1::Q1;
@@ -764,12 +789,21 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
         const int nplanes = p ? 2 * Q1 : Q1;
         const int k0 = p ? (2 * p - 1) * Q1 : 0;  // in-plane index of the stage's first population
         unsigned long long *b = bar + sb;
+        T *sbuf = buf + size_t(sb) * S::kStage;
         if constexpr (Coherent) fence_async_global();
         fence_async_shared();
-        if (lane == 0) mbar_arrive_expect_tx(b, unsigned(nplanes) * nbytes);
-        for (int k = lane; k < nplanes; k += 32)  // a pair stage of D1Q17 has 34 planes
-            bulk_copy_g2s(buf + size_t(sb) * S::kRows * SEG + size_t(k) * SEG + dst_off,
-                          fin + (long long)s.plane[cz * P2 + k0 + k] * a.stride + cs, nbytes, b);
+        if (tm) {  // one box per row group: d planes (library order) x SEG elements from g_al
+            if (lane == 0) {
+                mbar_arrive_expect_tx(b, unsigned(nplanes) * unsigned(SEG * sizeof(T)));
+                tma_load_2d(sbuf, tm, int(g_al), cz * P2 + k0, b);
+                if (p) tma_load_2d(sbuf + S::kGrp, tm, int(g_al), cz * P2 + k0 + Q1, b);
+            }
+        } else {
+            if (lane == 0) mbar_arrive_expect_tx(b, unsigned(nplanes) * nbytes);
+            for (int k = lane; k < nplanes; k += 32)  // a pair stage of D1Q17 has 34 planes
+                bulk_copy_g2s(sbuf + (k / Q1) * S::kGrp + (k % Q1) * SEG + dst_off,
+                              fin + (long long)s.plane[cz * P2 + k0 + k] * a.stride + cs, nbytes, b);
+        }
     };
     // the lane's pull by x-velocity a of a staged row sits at row + a SEG + tb - e_a; each
     // (plane, slot) is read by this lane only, so the lane may overwrite its own slots
@@ -804,7 +838,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
         parity ^= 1u << sb;
         pending &= ~(1u << sb);
         const int cz = st / S::kPerZ, p = st % S::kPerZ;
-        T *bs = buf + size_t(sb) * S::kRows * SEG;
+        T *bs = buf + size_t(sb) * S::kStage;
         if (active) {
             if (beyond) {
                 const int nrows = p ? 2 : 1;
@@ -820,7 +854,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
                                 v = t < 0 ? gl[i] : gr[i];
                             else
                                 v = load_pop<Coherent>(fin + (long long)s.plane[i] * a.stride + base + wrap(t, L));
-                            bs[(r * Q1 + av) * SEG + tb - e1<L1>(av)] = v;
+                            bs[r * S::kGrp + av * SEG + tb - e1<L1>(av)] = v;
                         }
                     }
                 });
@@ -836,7 +870,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
                 C::xrow(rowp, g);
                 C::yrest(g, h);
             } else {
-                const T *r1 = r0 + Q1 * SEG;
+                const T *r1 = r0 + S::kGrp;
                 auto rowm = [&](auto A) -> T {
                     constexpr int av = decltype(A)::value;
                     return r1[av * SEG - e1<L1>(av)];
@@ -892,8 +926,10 @@ SMRT_D void tp_warp_setup(unsigned char *dyn, unsigned long long *&bar, T *&buf)
 }
 
 // One step: warp w of block b takes the 32-cell tile b * (blockDim / 32) + w.
+// maps: tensor maps of the two states, used when a.tma is set (and the dynamic shared memory
+// is 128-byte aligned, as the boxes need).
 template <class L1, int N, class T, bool FixedX>
-__global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles) {
+__global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T> s;
     extern __shared__ __align__(128) unsigned char dyn[];
     unsigned long long *bar;
@@ -903,14 +939,15 @@ __global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles
     const int t = blockIdx.x * int(blockDim.x >> 5) + int(threadIdx.x >> 5);
     if (t >= ntiles) return;
     unsigned parity = 0u, pending = 0u;
-    tp_warp_tile<L1, N, T, FixedX, false>(a, s, a.fin, a.fout, t, buf, bar, parity, pending);
+    const CUtensorMap *tm = (a.tma && (smem_addr(dyn) & 127u) == 0u) ? &maps.src : nullptr;
+    tp_warp_tile<L1, N, T, FixedX, false>(a, s, a.fin, a.fout, t, buf, bar, parity, pending, tm);
 }
 
 // All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh); the
 // warps stride over the 32-cell tiles.
 template <class L1, int N, class T, bool FixedX>
 __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a, int nsteps, int ntiles,
-                                                                    unsigned *barg) {
+                                                                    unsigned *barg, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T> s;
     __shared__ int failed;
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -926,9 +963,11 @@ __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a,
     const unsigned step0 = __ldcg(&barg[2]);
     const T *src = a.fin;
     T *dst = a.fout;
+    const bool use_tma = a.tma && (smem_addr(dyn) & 127u) == 0u;
     for (int st = 0; st < nsteps; ++st) {
+        const CUtensorMap *tm = use_tma ? (src == a.fin ? &maps.src : &maps.dst) : nullptr;
         for (int t = blockIdx.x * wpb + int(threadIdx.x >> 5); t < ntiles; t += gridDim.x * wpb)
-            if (!tp_warp_tile<L1, N, T, FixedX, true>(a, s, src, dst, t, buf, bar, parity, pending)) {
+            if (!tp_warp_tile<L1, N, T, FixedX, true>(a, s, src, dst, t, buf, bar, parity, pending, tm)) {
                 failed = 1;
                 break;
             }
