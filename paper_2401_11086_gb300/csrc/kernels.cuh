@@ -225,9 +225,14 @@ struct Collide {
     // the constant a^gamma per monomial that does not vanish on the orbit.
     template <int Nm, class U>
     SMRT_D static void raw_moments(const U (&f)[Q], U (&R)[nmom(Nm)]) {
+        raw_moments_of<Nm>([&](auto I) { return f[decltype(I)::value]; }, R);
+    }
+    // ... with population i read as get(ic<i>) where it is needed (a pull, for the split step)
+    template <int Nm, class U, class Get>
+    SMRT_D static void raw_moments_of(Get &&get, U (&R)[nmom(Nm)]) {
         constexpr int Mm = nmom(Nm);
         static_for<Mm>([&](auto G) { R[decltype(G)::value] = U(0); });
-        R[0] = f[0];
+        R[0] = get(ic<0>{});
         static_for<kOrb.n>([&](auto O) {
             constexpr int o = decltype(O)::value;
             constexpr int np = 1 << (kOrb.k[o] - 1);
@@ -235,8 +240,9 @@ struct Collide {
             static_for<np>([&](auto B) {
                 constexpr int b = decltype(B)::value, p = kOrb.pair[o][b];
                 constexpr bool fl = kOrb.flip[o][b] != 0;
-                S[b] = f[2 * p + 1] + f[2 * p + 2];
-                D[b] = fl ? f[2 * p + 2] - f[2 * p + 1] : f[2 * p + 1] - f[2 * p + 2];
+                const U fp = get(ic<2 * p + 1>{}), fm = get(ic<2 * p + 2>{});
+                S[b] = fp + fm;
+                D[b] = fl ? fm - fp : fp - fm;
             });
             wht<np>(S);
             wht<np>(D);
@@ -422,9 +428,8 @@ struct Collide {
     SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const double (&wpd)[NP + 1], T c,
                                double cd, const T *tauA, const T *tauB, unsigned key = 0u) {
         if constexpr (Split) {
-            Acc fa[Q];
-            static_for<Q>([&](auto I) { fa[decltype(I)::value] = widen<Acc>(f[decltype(I)::value]); });
-            return collide_split(fa, f, wp, wpd, c, cd, tauA, tauB, key);
+            return collide_split([&](auto I) { return widen<Acc>(f[decltype(I)::value]); },
+                                 [&](int i, T v) { f[i] = v; }, wp, wpd, c, cd, tauA, tauB, key);
         } else {
             // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
             T v[M], Rc[M];
@@ -450,16 +455,19 @@ struct Collide {
         }
     }
 
-    // Split precision (T float, Acc double): fa = the pulled populations in Acc (exact end-state
-    // values at ghost slots), f = the post-collision populations, rounded stochastically to T.
+    // Split precision (T float, Acc double): pull(ic<i>) = pulled population i in Acc (exact
+    // end-state values at ghost slots), read once; store(i, value) receives post-collision
+    // population i, rounded stochastically to T, as soon as it is formed (no array of either
+    // is held, which keeps the live registers down).
     // In Acc: the raw moments, the conserved moments, the absolute coefficients and the
     // equilibrium they are reduced by, and the rebuild of the equilibrium with the weights and c
     // in Acc; in T: the non-equilibrium remainder through a4-a6 and its rebuild.
-    SMRT_D static bool collide_split(const Acc (&fa)[Q], T (&f)[Q], const T (&wp)[NP + 1],
+    template <class Pull, class Store>
+    SMRT_D static bool collide_split(Pull &&pull, Store &&store, const T (&wp)[NP + 1],
                                      const double (&wpd)[NP + 1], T c, double cd, const T *tauA,
                                      const T *tauB, unsigned key) {
         Acc Ra[M], va[M], teq[M], raw[5];
-        raw_moments<N>(fa, Ra);
+        raw_moments_of<N>(pull, Ra);
         raw[0] = Ra[0];
         raw[1] = Ra[mi_pos(1, 0, 0)];
         raw[2] = Ra[mi_pos(0, 1, 0)];
@@ -496,7 +504,7 @@ struct Collide {
         const Acc C = c2 * c2 * (-m[4] - Acc(3) * A / c2) / Acc(6);
         const Acc corr[5] = {A - C * Acc(3) / c2, -c2 * m[1], -c2 * m[2], -c2 * m[3], C};
         rebuild_emit(teq, Acc(cd), wpd, [&](int i, Acc v) {
-            f[i] = round_stochastic(v + widen<Acc>(oneq[i]), key ^ (0x9e3779b9u * unsigned(i + 1)));
+            store(i, round_stochastic(v + widen<Acc>(oneq[i]), key ^ (0x9e3779b9u * unsigned(i + 1))));
         }, corr);
         return ok;
     }
@@ -589,27 +597,28 @@ SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *_
             return widen<V>(load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L)));
         }
     };
-    V fv[Lat::Q];
-    fv[0] = pull(0, x - in.kx);  // the rest population streams by k as well
-    static_for<Lat::NP>([&](auto P) {
-        constexpr int p = decltype(P)::value;
-        fv[2 * p + 1] = pull(2 * p + 1, x - (Lat::e(p, 0) + in.kx));
-        fv[2 * p + 2] = pull(2 * p + 2, x - (-Lat::e(p, 0) + in.kx));
-    });
-    T f[Lat::Q];
-    bool ok;
-    if constexpr (Split)
-        ok = C::collide_split(fv, f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
-                              mix32(unsigned(base + x) ^ mix32(step)));
-    else
-        ok = C::collide(fv, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
-                        mix32(unsigned(base + x) ^ mix32(step)));
-    if constexpr (!Split) static_for<Lat::Q>([&](auto I) { f[decltype(I)::value] = fv[decltype(I)::value]; });
-    if (!ok) atomicOr(a.health, 1u);
-    static_for<Lat::Q>([&](auto I) {
+    // x-distance of population i's pull: the rest population streams by k as well
+    auto src_x = [&](auto I) {
         constexpr int i = decltype(I)::value;
-        fout[a.plane[i] + base + x] = f[i];
-    });
+        constexpr int ex = i == 0 ? 0 : ((i & 1) ? Lat::e((i - 1) / 2, 0) : -Lat::e((i - 1) / 2, 0));
+        return x - (ex + in.kx);
+    };
+    bool ok;
+    if constexpr (Split) {
+        ok = C::collide_split([&](auto I) { return pull(decltype(I)::value, src_x(I)); },
+                              [&](int i, T v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wpd, a.c,
+                              a.cd, tau_a<T>(in), tau_b<T>(in), mix32(unsigned(base + x) ^ mix32(step)));
+    } else {
+        T f[Lat::Q];
+        static_for<Lat::Q>([&](auto I) { f[decltype(I)::value] = pull(decltype(I)::value, src_x(I)); });
+        ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
+                        mix32(unsigned(base + x) ^ mix32(step)));
+        static_for<Lat::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            fout[a.plane[i] + base + x] = f[i];
+        });
+    }
+    if (!ok) atomicOr(a.health, 1u);
 }
 
 template <class Lat, int N, class T, class Acc, bool Split, bool FixedX>

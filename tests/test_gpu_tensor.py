@@ -200,9 +200,11 @@ def test_caller_velocity_order_is_free(lat, width):
     nx, N = 64, 4
     case, h = _oracle_case(olat, N, 3.0, nx)
     left, right = P.lb_rankine_hugoniot(3.0, theta1=case.theta1)
+    w_oracle_order = np.empty(olat.q)
+    w_oracle_order[idx] = d.w  # the same weights and c in both contexts, only the order differs
     outs = []
     for desc, order in ((_desc(d, (2, 0, 0)), idx),
-                        (P.LatticeDesc(e=olat.e.astype(np.int8), w=olat.w, c=olat.c, degree=11,
+                        (P.LatticeDesc(e=olat.e.astype(np.int8), w=w_oracle_order, c=d.c, degree=11,
                                        shift=(2, 0, 0)), np.arange(olat.q))):
         ctx = P.lb_init_lattice(desc, nx, N=N, precision="f64", bc_x=1)
         P.lb_set_relaxation(ctx, _tau(case.model), True, 1.0, left, right)
