@@ -738,7 +738,6 @@ struct TPWarpStage {
     static constexpr int kAlign = 16 / int(sizeof(T));  // elements per 16 bytes
     static constexpr int kEmax = L1::E(L1::NP1 - 1);    // largest |e| of the 1D rule
     static constexpr int kSeg = kW + ((2 * kEmax + kAlign - 1) + kAlign - 1) / kAlign * kAlign;
-    static constexpr int kRows = 2 * L1::Q1;            // planes of the largest stage
     // a stage buffer holds two groups of d rows (the +e_b and -e_b x-rows), each group
     // starting 128-byte aligned so that one tensor-map box fills it
     static constexpr int kGrp = int((L1::Q1 * kSeg * sizeof(T) + 127) / 128 * 128 / sizeof(T));
