@@ -81,17 +81,22 @@ struct TPMaps {
 template <class L1, class T>
 struct TPTables {
     static constexpr int Q = L1::Q1 * L1::Q1 * L1::Q1;
+    static constexpr int kPow = 6;  // powers e^0 .. e^5 (N <= 5)
     int plane[Q];
     T e[L1::Q1];
     T w[L1::Q1];
+    T pw[L1::Q1][kPow];  // e_a^k: the y and z passes read them instead of forming them per cell
 };
 
 template <class L1, class T, class U>
 SMRT_D void tp_load_tables(const TPArgs<T> &a, TPTables<L1, U> &s) {
     for (int i = threadIdx.x; i < TPTables<L1, U>::Q; i += blockDim.x) s.plane[i] = a.plane_idx[i];
     if (threadIdx.x < L1::Q1) {
-        s.e[threadIdx.x] = U(e1<L1>(threadIdx.x));
+        const U ea = U(e1<L1>(threadIdx.x));
+        s.e[threadIdx.x] = ea;
         s.w[threadIdx.x] = U(a.w1[threadIdx.x]);
+        U p = U(1);
+        for (int k = 0; k < TPTables<L1, U>::kPow; ++k, p *= ea) s.pw[threadIdx.x][k] = p;
     }
     __syncthreads();
 }
@@ -221,6 +226,11 @@ struct TPCell {
         T pw[N + 1];
         pw[0] = T(1);
         static_for<N>([&](auto K) { pw[decltype(K)::value + 1] = pw[decltype(K)::value] * eb; });
+        ypair_pw(gp, gm, pw, h);
+    }
+    // ... with the powers e_b^k given (pw[k], k <= N, e.g. a shared-memory table row)
+    template <class PW>
+    SMRT_D static void ypair_pw(const T (&gp)[N + 1], const T (&gm)[N + 1], const PW &pw, T (&h)[N + 1][N + 1]) {
         static_for<N + 1>([&](auto J) {
             constexpr int j = decltype(J)::value;
             const T s = gp[j] + gm[j], d = gp[j] - gm[j];
@@ -236,6 +246,10 @@ struct TPCell {
         T pw[N + 1];
         pw[0] = T(1);
         static_for<N>([&](auto L) { pw[decltype(L)::value + 1] = pw[decltype(L)::value] * ec; });
+        zfold_pw(h, pw, R);
+    }
+    template <class PW>
+    SMRT_D static void zfold_pw(T (&h)[N + 1][N + 1], const PW &pw, T (&R)[M]) {
         static_for<M>([&](auto G) {
             constexpr int g = decltype(G)::value;
             constexpr int j = mi_comp(g, 0), k = mi_comp(g, 1), l = mi_comp(g, 2);
@@ -254,6 +268,10 @@ struct TPCell {
         U pw[N + 1];
         pw[0] = U(1);
         static_for<N>([&](auto L) { pw[decltype(L)::value + 1] = pw[decltype(L)::value] * ec; });
+        zplane_pw(P, pw, Pc);
+    }
+    template <class U, class PW>
+    SMRT_D static void zplane_pw(const U (&P)[M], const PW &pw, U (&Pc)[N + 1][N + 1]) {
         static_for<N + 1>([&](auto J) {
             constexpr int j = decltype(J)::value;
             static_for<N + 1 - j>([&](auto K) {
@@ -273,6 +291,10 @@ struct TPCell {
         U pw[N + 1];
         pw[0] = U(1);
         static_for<N>([&](auto K) { pw[decltype(K)::value + 1] = pw[decltype(K)::value] * eb; });
+        yrows_pw(Pc, pw, Pp, Pm);
+    }
+    template <class U, class PW>
+    SMRT_D static void yrows_pw(const U (&Pc)[N + 1][N + 1], const PW &pw, U (&Pp)[N + 1], U (&Pm)[N + 1]) {
         static_for<N + 1>([&](auto J) {
             constexpr int j = decltype(J)::value;
             U ev = Pc[j][0], od = U(0);
@@ -760,6 +782,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
                          unsigned &pending, const CUtensorMap *tm) {
     using C = TPCell<L1, N, T>;
     using S = TPWarpStage<L1, T>;
+    static_assert(N + 1 <= TPTables<L1, T>::kPow, "the powers table holds e^0 .. e^5");
     constexpr int Q1 = L1::Q1;
     constexpr int NP1 = L1::NP1;
     constexpr int P2 = Q1 * Q1;
@@ -877,9 +900,9 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
                 T gp[N + 1], gm[N + 1];
                 C::xrow(rowp, gp);
                 C::xrow(rowm, gm);
-                C::ypair(gp, gm, s.e[2 * p - 1], h);
+                C::ypair_pw(gp, gm, s.pw[2 * p - 1], h);
             }
-            if (p == NP1) C::zfold(h, s.e[cz], R);
+            if (p == NP1) C::zfold_pw(h, s.pw[cz], R);
         }
         __syncwarp();  // every lane is done with buffer sb
         if (st + NS < S::kTotal) issue(st + NS);
@@ -892,7 +915,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
 #pragma unroll 1
         for (int cz = 0; cz < Q1; ++cz) {
             T Pc[N + 1][N + 1];
-            C::template zplane<T>(R, s.e[cz], Pc);
+            C::template zplane_pw<T>(R, s.pw[cz], Pc);
             const T wc = s.w[cz];
             {
                 T Pb[N + 1];
@@ -902,7 +925,7 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
 #pragma unroll 1
             for (int p = 1; p <= NP1; ++p) {
                 T Pp[N + 1], Pm[N + 1];
-                C::template yrows<T>(Pc, s.e[2 * p - 1], Pp, Pm);
+                C::template yrows_pw<T>(Pc, s.pw[2 * p - 1], Pp, Pm);
                 const T wbc = wc * s.w[2 * p - 1];
                 C::template emit_x<T>(Pp, wbc, s.w, cz * P2 + (2 * p - 1) * Q1, put);
                 C::template emit_x<T>(Pm, wbc, s.w, cz * P2 + 2 * p * Q1, put);
