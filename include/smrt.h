@@ -103,7 +103,11 @@ typedef struct {
  *     batched 1D lines (ny = nz = 1), frame shift along x only, LB_F64 or LB_F32; weights
  *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint. The states
  *     passed to the stepping calls must start on 16-byte boundaries (LB_ERR_INVALID
- *     otherwise): the kernel stages population segments with the bulk-copy engine.
+ *     otherwise): the kernel stages population segments with the bulk-copy engine. When e
+ *     lists the velocities in the library order (i = a + d b + d^2 c over the 1D order rest,
+ *     +1, -1, +2, -2, ..., the order lb_lattice_named returns), each group of d planes is
+ *     staged as one box of a 2D tensor map of the state; any other order works, staged plane
+ *     by plane, with the same results bit for bit.
  * hermite_order N: truncation order of Eqs. an/fi.
  * cuda_stream: cudaStream_t used for every later call on this context.
  * On success *out is a new context (relaxation times unset: lb_set_relaxation must follow).
