@@ -39,6 +39,7 @@ METRIC = "GLUPSxQ (cell-velocity updates/s) and % HBM roofline"
 UNIT = "G cell-velocity updates/s"
 KERNEL_SOURCES = ["core.cuh", "kernels.cuh", "lattices.cuh", "dispatch.h"]
 PROFILE = os.path.join(ROOT, "profiles", "collide_stream_d3q39_f32_box.txt")
+PROFILE_BATCHED = os.path.join(ROOT, "profiles", "collide_stream_d3q103_n4_batched.txt")
 
 
 def kernel_hash() -> str:
@@ -57,13 +58,13 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-def profile_traffic(n: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to n^3 cells, or None
-    when the summary is missing or was taken on different kernel sources."""
-    if not os.path.exists(PROFILE):
+def profile_value(path: str, key: str):
+    """A number recorded in a committed ncu summary ("key: value" line), or None when the
+    summary is missing or was taken on different kernel sources."""
+    if not os.path.exists(path):
         return None
     vals = {}
-    with open(PROFILE) as fh:
+    with open(path) as fh:
         for line in fh:
             if ":" in line:
                 k, v = line.split(":", 1)
@@ -71,10 +72,15 @@ def profile_traffic(n: int):
     if vals.get("kernel_sources_sha256_12") != kernel_hash():
         return None
     try:
-        per_cell = float(vals["dram_bytes_per_cell"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
-    return per_cell * n ** 3
+
+
+def profile_traffic(n: int):
+    """DRAM bytes per launch from the committed ncu summary of the box, scaled to n^3 cells."""
+    per_cell = profile_value(PROFILE, "dram_bytes_per_cell")
+    return None if per_cell is None else per_cell * n ** 3
 
 
 def tau_table():
@@ -315,7 +321,8 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
                        "schedule": sched,
                        "l2": "L2 flushed (256 MB write) before every timed step; steps timed one by one"},
             "roofline": {"bound": "alu", "achieved": gflop, "peak": FP64_PEAK_GFLOPS,
-                         "unit": "GFLOP/s (fp64)", "frac": gflop / FP64_PEAK_GFLOPS, "traffic": None,
+                         "unit": "GFLOP/s (fp64)", "frac": gflop / FP64_PEAK_GFLOPS,
+                         "traffic": profile_value(PROFILE_BATCHED, "dram_bytes_per_launch"),
                          "peak_kind": "nominal FP64 rate", "flop_per_cell": BATCHED_FP64_FLOP_PER_CELL,
                          "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak,
                          "note": "double-precision arithmetic, not HBM, limits this workload"},
