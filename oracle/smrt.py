@@ -44,8 +44,11 @@ ES-BGK (Model.es_b set): step 3 instead relaxes every order n >= 2 at the single
 toward the local-frame coefficients of Holway's anisotropic Gaussian (``es_target``).
 
 Parity: pinned (conservation, equilibrium fixed point, BGK reduction against an independent
-regularised-BGK formula, single-mode decay, Rankine-Hugoniot steady shock; for ES-BGK the
-target against direct numerical integration of the Gaussian, b = 0 against BGK, Pr = 1/(1-b)).
+regularised-BGK formula, single-mode decay, the Maxwell-molecule law mu = p tau_c proportional
+to theta at every density measured from one collision, sigma and q of ``macroscopic`` against
+their direct moments, Rankine-Hugoniot steady shock with uniform face fluxes of mass,
+momentum and energy; for ES-BGK the target against direct numerical integration of the
+Gaussian, b = 0 against BGK, Pr = 1/(1-b)).
 """
 from __future__ import annotations
 

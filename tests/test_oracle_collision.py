@@ -345,3 +345,120 @@ def test_es_collision_conserves(lats):
     h = S.collide(f, S.Model(lat, 5, tau_ref=0.7, es_b=-0.5))
     for a, b in zip(S.conserved(f, lat), S.conserved(h, lat)):
         np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------- Maxwell molecules
+def _measured_viscosity(lat, model, rho, theta, u=(0.2, -0.1, 0.05), eps=1e-4):
+    """mu = p tau_c of a pure shear mode (the (2,0) component d_xy), with tau_c read off one
+    collision: the mode is multiplied by 1 - 1/tau and tau = tau_c + 1/2 (second-order scheme).
+    Nothing here calls the oracle's relaxation-time formula."""
+    N = model.N
+    al = H.multi_indices_upto(N)
+    k0 = al.index((1, 1, 0))
+    d = np.zeros((len(al), 1))
+    d[0, 0] = rho
+    d[k0, 0] = eps * rho
+    uu = np.array(u, dtype=float)[:, None]
+    f = S.rebuild(S.to_absolute(d, N, uu, np.array([theta])), lat, N)
+    dh = S.local_direct(S.collide(f, model), lat, N, uu, np.array([theta]))
+    lam = dh[k0, 0] / d[k0, 0]
+    tau_c = 1.0 / (1.0 - lam) - 0.5
+    return rho * theta * tau_c
+
+
+def _viscosity_law_error(lat, model):
+    """Largest relative departure of the measured mu(rho, theta) from mu = mu_ref theta: the
+    viscosity of Maxwell molecules is proportional to the temperature and independent of the
+    density (Sec. 4.2), mu_ref being the value at rho_ref and theta = 1."""
+    mu_ref = _measured_viscosity(lat, model, model.rho_ref, 1.0)
+    err = 0.0
+    for rho in (0.5, 1.0, 2.0, 3.7):
+        for theta in (0.8, 1.0, 1.2):
+            mu = _measured_viscosity(lat, model, rho, theta)
+            err = max(err, abs(mu / (mu_ref * theta) - 1.0))
+    return err, mu_ref
+
+
+@pytest.mark.parametrize("rho_ref", [1.0, 1.5])
+def test_maxwell_molecule_viscosity_law(lats, rho_ref):
+    """Maxwell molecules (Sec. 4.2; viscosity proportional to temperature): the shear viscosity
+    measured from one collision is mu = p tau_c = rho_ref tau_ref theta at every density; at the
+    reference density and theta = 1 the continuous time is tau_ref itself."""
+    lat = lats["D3Q39"]
+    model = S.Model(lat, 3, tau_ref=1.3, rho_ref=rho_ref)
+    err, mu_ref = _viscosity_law_error(lat, model)
+    assert err < 1e-9
+    assert abs(mu_ref - rho_ref * 1.3) < 1e-9
+
+
+def test_viscosity_law_detects_an_inverted_density_ratio(lats, monkeypatch):
+    """The pin above fails when the oracle scales tau by rho/rho_ref instead of rho_ref/rho
+    (the mistake planted in the oracle on the CPU), and also with the density law switched off
+    (mu would then grow with rho)."""
+    lat = lats["D3Q39"]
+
+    def inverted(model, rho):
+        return {nm: model.tau_star[nm] * model.tau_ref * (rho / model.rho_ref) + 0.5
+                for nm in model.tau_star}
+    monkeypatch.setattr(S, "tau_discrete", inverted)
+    err, _ = _viscosity_law_error(lat, S.Model(lat, 3, tau_ref=1.3))
+    assert err > 1.0
+    monkeypatch.undo()
+    err, _ = _viscosity_law_error(lat, S.Model(lat, 3, tau_ref=1.3, maxwell_law=False))
+    assert err > 1.0
+
+
+# ---------------------------------------------------------------------------- stress and heat flux
+def _sigma_q_error(lat, N, macroscopic, seed=3):
+    """Largest difference between macroscopic()'s sigma and q and their definitions as direct
+    moments of the populations (Sec. 2.2): with the peculiar velocity c_i = xi_i + u_bar - u,
+    sigma = sum_i f_i c_i c_i - p delta (p = rho theta) and q = 1/2 sum_i f_i |c_i|^2 c_i. A
+    one-cell periodic grid makes streaming the identity, so the populations are f itself."""
+    rng = np.random.default_rng(seed)
+    err = 0.0
+    for k in range(3):
+        rho = 0.8 + 0.5 * rng.random(1)
+        u = 0.3 * rng.standard_normal((3, 1))
+        th = 0.7 + 0.6 * rng.random(1)
+        f = S.equilibrium(rho, u, th, lat, N)
+        f = f * (1.0 + 0.2 * rng.standard_normal(f.shape))
+        shift = (k, 0, 0)
+        geom = S.Geometry(shape=(1, 1, 1), shift=shift)
+        m = macroscopic(f.reshape(lat.q, 1, 1, 1), S.Model(lat, N, tau_ref=1.0), geom)
+        ubar = lat.c * np.asarray(shift, dtype=float)
+        vel = lat.xi + ubar[None, :]                       # physical velocities
+        fc = f[:, 0]
+        rho_d = fc.sum()
+        u_d = (fc[:, None] * vel).sum(0) / rho_d
+        c = vel - u_d[None, :]
+        p_d = (fc * (c * c).sum(1)).sum() / 3.0
+        S2 = np.einsum("i,ik,il->kl", fc, c, c) - p_d * np.eye(3)
+        q_d = 0.5 * np.einsum("i,i,ik->k", fc, (c * c).sum(1), c)
+        pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        sig_d = np.array([S2[a, b] for a, b in pairs])
+        scale = max(1.0, np.abs(sig_d).max(), np.abs(q_d).max())
+        err = max(err, abs(m["theta"][0] * m["rho"][0] - p_d) / scale,
+                  np.abs(m["sigma"][:, 0] - sig_d).max() / scale,
+                  np.abs(m["q"][:, 0] - q_d).max() / scale)
+    return err
+
+
+@pytest.mark.parametrize("name,N", [("D3Q39", 3), ("D3Q103", 4), ("D3Q729", 5)])
+def test_macroscopic_stress_and_heat_flux_are_direct_moments(lats, name, N):
+    assert _sigma_q_error(lats[name], N, S.macroscopic) < 1e-12
+
+
+@pytest.mark.parametrize("mutation", ["sigma_theta_squared", "q_theta_half", "q_without_half"])
+def test_stress_and_heat_flux_pin_detects_mistakes(lats, mutation):
+    """Plausible mistakes in macroscopic() (a wrong power of theta in sigma or q, the 1/2 of q
+    dropped), planted in a wrapper around the oracle, fail the direct-moment pin."""
+    def planted(h, model, geom):
+        m = dict(S.macroscopic(h, model, geom))
+        if mutation == "sigma_theta_squared":
+            m["sigma"] = m["sigma"] * m["theta"]
+        elif mutation == "q_theta_half":
+            m["q"] = m["q"] / m["theta"]
+        else:
+            m["q"] = 2.0 * m["q"]
+        return m
+    assert _sigma_q_error(lats["D3Q39"], 3, planted) > 1e-3

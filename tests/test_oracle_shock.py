@@ -56,13 +56,15 @@ def converged_shock():
     for _ in range(1900):
         h = S.step(h, case.model, case.geom)
     m_prev = S.macroscopic(h, case.model, case.geom)
-    for _ in range(100):
+    for _ in range(99):
         h = S.step(h, case.model, case.geom)
-    return case, S.macroscopic(h, case.model, case.geom), m_prev
+    h_before = h
+    h = S.step(h, case.model, case.geom)
+    return case, S.macroscopic(h, case.model, case.geom), m_prev, h_before, h
 
 
 def test_converged_shock_is_steady_and_satisfies_rankine_hugoniot(converged_shock):
-    case, m, m_prev = converged_shock
+    case, m, m_prev = converged_shock[:3]
     st = case.states
     assert case.k == 1 and abs(case.model.tau_ref - 2 * np.sqrt(1.5)) < 1e-12
     # steady: density changes by < 1e-5 over the last 100 steps
@@ -82,6 +84,90 @@ def test_converged_shock_is_steady_and_satisfies_rankine_hugoniot(converged_shoc
     # the profile is monotone and the heat flux inside the shock is negative (flows upstream)
     assert np.all(np.diff(m["rho"]) > -1e-9)
     assert m["q"][0][pos] < 0.0
+
+
+def _face_fluxes(case, h, phi):
+    """Discrete flux of the quantity phi_i through every x face (face j between cells j-1 and
+    j, j = 0..nx) during one streaming: each post-collision population h_i at x' hops
+    s_i = e_ix + k_x cells, so it crosses the faces between x' and x' + s_i, carrying c phi_i
+    h_i (cell size c). Cells beyond the ends hold the fixed end-state populations."""
+    lat = case.model.lat
+    nx = case.geom.shape[2]
+    hops = lat.e[:, 0].astype(int) + case.k
+    R = int(np.abs(hops).max())
+    F = np.zeros(nx + 1)
+    for i in range(lat.q):
+        row = np.concatenate([np.full(R, case.geom.ghost_left[i]), h[i, 0, 0, :],
+                              np.full(R, case.geom.ghost_right[i])])
+        s = hops[i]
+        for j in range(nx + 1):
+            if s > 0:        # from cells j-s .. j-1, rightwards
+                F[j] += lat.c * phi[i] * row[R + j - s:R + j].sum()
+            elif s < 0:      # from cells j .. j-s-1, leftwards
+                F[j] -= lat.c * phi[i] * row[R + j:R + j - s].sum()
+    return F
+
+
+def _rh_fluxes(st, side):
+    """Mass, x-momentum and energy fluxes of a uniform Maxwellian state (monatomic, D = 3)."""
+    rho, u, th = st["rho" + side], st["u" + side], st["theta" + side]
+    return {"mass": rho * u, "momentum": rho * u * u + rho * th,
+            "energy": rho * u * (0.5 * u * u + 2.5 * th)}
+
+
+def test_converged_shock_conserves_fluxes_face_by_face(converged_shock):
+    """Eq. rankine: in the steady shock the discrete fluxes of mass, x-momentum and energy
+    through every face are equal, and equal to the Rankine-Hugoniot fluxes of either end state.
+    The face fluxes are counted from the populations themselves; the change of each cell's
+    content over the last step equals its net face flux (the step's exact conservation)."""
+    case, _, _, h_before, h = converged_shock
+    st = case.states
+    lat = case.model.lat
+    vel = lat.c * (lat.e.astype(float) + np.array([case.k, 0, 0]))
+    phis = {"mass": np.ones(lat.q), "momentum": vel[:, 0], "energy": 0.5 * (vel ** 2).sum(1)}
+    up, down = _rh_fluxes(st, "1"), _rh_fluxes(st, "2")
+    for name, phi in phis.items():
+        # the two end states carry equal fluxes: the jump conditions themselves
+        assert abs(down[name] / up[name] - 1.0) < 1e-12
+        F = _face_fluxes(case, h_before, phi)
+        content_before = lat.c * (phi @ h_before[:, 0, 0, :])
+        content_after = lat.c * (phi @ h[:, 0, 0, :])
+        np.testing.assert_allclose(F[:-1] - F[1:], content_after - content_before, atol=1e-13)
+        assert np.abs(F / up[name] - 1.0).max() < 1e-6, name
+
+
+def _cell_fluxes(case, m, tau_of=S.tau_discrete):
+    """Fluxes from the cell moments of macroscopic(): mass rho u; momentum rho u^2 + p +
+    sigma_xx; energy rho u (u^2/2 + 5 theta/2) + sigma_xx u + q_x. With the second-order time
+    discretisation the stress and heat flux that the fluxes carry are the averages over one
+    collision of the pre- and post-collision values, i.e. the pre-collision sigma and q scaled
+    by 1 - 1/(2 tau_20) and 1 - 1/(2 tau_31) (q is the trace part of order 3, relaxed at
+    tau_31)."""
+    rho, u, th = m["rho"], m["u"][0], m["theta"]
+    tau = tau_of(case.model, rho)
+    sxx = (1.0 - 0.5 / tau[(2, 0)]) * m["sigma"][0]
+    qx = (1.0 - 0.5 / tau[(3, 1)]) * m["q"][0]
+    return {"mass": rho * u, "momentum": rho * u * u + rho * th + sxx,
+            "energy": rho * u * (0.5 * u * u + 2.5 * th) + sxx * u + qx}
+
+
+def test_converged_shock_cell_fluxes_from_stress_and_heat_flux(converged_shock):
+    """Inside the shock sigma_xx and q_x carry a few percent of the momentum and energy
+    fluxes; the fluxes formed from macroscopic()'s moments stay uniform to the discretisation
+    error (3.5e-5 here), while a wrong power of theta in sigma or q, or a dropped 1/2 in q,
+    moves them by more than 3e-4."""
+    case, m = converged_shock[:2]
+    up = _rh_fluxes(case.states, "1")
+    J = _cell_fluxes(case, m)
+    assert np.abs(m["sigma"][0]).max() > 0.02 and np.abs(m["q"][0]).max() > 0.02
+    for name in ("mass", "momentum", "energy"):
+        assert np.abs(J[name] / up[name] - 1.0).max() < 1e-4, name
+    for key, scale in (("sigma", m["theta"]), ("q", 1.0 / m["theta"]), ("q", 2.0)):
+        bad = dict(m)
+        bad[key] = m[key] * scale
+        Jb = _cell_fluxes(case, bad)
+        worst = max(np.abs(Jb[n] / up[n] - 1.0).max() for n in ("momentum", "energy"))
+        assert worst > 3e-4, key
 
 
 def _upstream_noise_growth(Ma, steps=600):
