@@ -80,9 +80,11 @@ StepArgs<Lat, T> make_args(const CtxView &v, const void *fin, void *fout) {
     for (int p = 0; p <= Lat::NP; ++p) {
         a.wp[p] = T(v.wp[p]);
         a.wpd[p] = v.wp[p];
+        a.wlo[p] = float(v.wp[p] - double(float(v.wp[p])));
     }
     a.c = T(v.c);
     a.cd = v.c;
+    a.clo = float(v.c - double(float(v.c)));
     a.nx = v.nx;
     a.ny = v.ny;
     a.nz = v.nz;

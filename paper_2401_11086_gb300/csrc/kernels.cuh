@@ -68,8 +68,10 @@ struct StepArgs {
     long long plane[Lat::Q];  // element offset of each population plane, library order
     T wp[Lat::NP + 1];        // weight of the rest velocity, then of each pair
     double wpd[Lat::NP + 1];  // the same weights in double, for every double-precision rebuild
+    float wlo[Lat::NP + 1];   // w - float(w): the weights as two-float numbers (split precision)
     T c;
     double cd;                // c in double
+    float clo;                // c - float(c)
     int nx, ny, nz;           // box kernel geometry
     int kx, ky, kz;           // box kernel frame shift
     unsigned step;            // step counter (stochastic rounding of the split precision)
@@ -122,10 +124,142 @@ SMRT_D float round_stochastic(double x, unsigned key) {
     return __uint_as_float(y);
 }
 
+// ------------------------------------------------------------------------------ two-float
+// Unevaluated sums hi + lo of two floats (about 48 significant bits) built from error-free
+// transformations: Knuth's two-sum (a + b and its rounding error in six additions) and the
+// product with its rounding error from one fused multiply-add. The split-precision step uses
+// them, on the single-precision pipe, wherever it needs more than a float's 24 bits. The
+// __f*_rn intrinsics are never contracted into fused operations by the compiler, which these
+// transformations rely on.
+struct ff {
+    float hi, lo;
+};
+SMRT_D ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+SMRT_D ff ff_quick(float a, float b) {  // two-sum when |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+SMRT_D ff operator+(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+SMRT_D ff operator-(ff a) { return {-a.hi, -a.lo}; }
+SMRT_D ff operator-(ff a, ff b) { return a + (-b); }
+SMRT_D ff operator+(ff a, float b) {
+    const ff s = ff_two_sum(a.hi, b);
+    return ff_quick(s.hi, __fadd_rn(s.lo, a.lo));
+}
+SMRT_D ff operator*(ff a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    return ff_quick(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+SMRT_D ff operator*(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_quick(p, e);
+}
+SMRT_D ff ff_div(ff a, ff b) {  // one correction step after the float quotient
+    const float r = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    const ff rem = a - b * q1;
+    return ff_quick(q1, __fmul_rn(rem.hi, r));
+}
+
+// 1/n as a two-float number (the double quotient split in two floats, about 2^-50)
+template <int n>
+SMRT_D ff ff_inv() {
+    constexpr float hi = float(1.0 / n);
+    constexpr float lo = float(1.0 / n - double(hi));
+    return ff{hi, lo};
+}
+
+// Fixed point: x 2^S rounded to the nearest integer (ties away from zero), formed from the
+// float's bit pattern with integer instructions. Sums of such integers are exact and
+// independent of their order. Valid for |x| < 2^(62 - S); magnitudes below 2^-(S + 1) give 0,
+// as do zeros and subnormals. The split-precision step keeps populations and raw moments at
+// S = kFix (2^-44 resolution, range 2^19) and the equilibrium's monomial coefficients at
+// S = kFixP (2^-48, range 2^14).
+constexpr int kFix = 44;
+constexpr int kFixP = 48;
+template <int S = kFix>
+SMRT_D long long to_fixed(float x) {
+    const unsigned b = __float_as_uint(x);
+    const int e = int((b >> 23) & 0xffu);
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // |x| = m 2^(e - 150)
+    const int s = e - 150 + S;
+    unsigned long long mag;
+    if (s >= 0) {
+        mag = m << (s < 39 ? s : 39);
+    } else {
+        const int r = -s < 31 ? -s : 31;
+        mag = (m + (1ull << (r - 1))) >> r;
+    }
+    if (e == 0) mag = 0;
+    const long long q = static_cast<long long>(mag);
+    return (b >> 31) ? -q : q;
+}
+template <int S = kFix>
+SMRT_D long long to_fixed(double x) {
+    return __double2ll_rn(x * static_cast<double>(1ull << S));
+}
+// Exact sum of products m x (m a small positive constant, x a 64-bit integer) in one 64-bit
+// accumulator, each product formed as m lo32(x) (a 32 x 32 -> 64-bit multiply-add) plus
+// m hi32(x) added to the upper word. Arithmetic is modulo 2^64, so the sum is exact whenever it
+// fits in 64 bits.
+struct SplitAcc {
+    unsigned long long v = 0;
+    template <int m>
+    SMRT_D void madd(long long x) {
+        static_assert(m > 0, "positive multiplier");
+        const unsigned long long ux = static_cast<unsigned long long>(x);
+        v += static_cast<unsigned long long>(static_cast<unsigned>(ux)) * static_cast<unsigned>(m);
+        v += static_cast<unsigned long long>(static_cast<unsigned>(ux >> 32) * static_cast<unsigned>(m)) << 32;
+    }
+    SMRT_D void add(long long x) { v += static_cast<unsigned long long>(x); }
+    SMRT_D long long value() const { return static_cast<long long>(v); }
+};
+
+// q 2^-S as a two-float number: q = a 2^48 + b 2^24 + c with 0 <= b, c < 2^24, each piece
+// exact as a float
+constexpr float pow2f(int e) { return e >= 0 ? float(1ull << e) : 1.0f / float(1ull << -e); }
+template <int S = kFix>
+SMRT_D ff fixed_to_ff(long long q) {
+    const float a = float(int(q >> 48)) * pow2f(48 - S);
+    const float b = float(int((q >> 24) & 0xffffff)) * pow2f(24 - S);
+    const float c = float(int(q & 0xffffff)) * pow2f(-S);
+    const ff s = ff_two_sum(a, b);
+    return ff_quick(s.hi, __fadd_rn(s.lo, c));
+}
+
+// Stochastic rounding of a two-float value hi + lo (|lo| at most half a float spacing of hi) to
+// a float: hi's neighbour on lo's side with probability |lo| / (distance to that neighbour),
+// else hi, drawn from the same counter-based hash as above.
+SMRT_D float round_stochastic(ff x, unsigned key) {
+    const unsigned hb = __float_as_uint(x.hi);
+    const bool away = (x.lo > 0.f) == (x.hi > 0.f);  // the neighbour of larger magnitude
+    const float nb = __uint_as_float(away ? hb + 1u : hb - 1u);
+    const float gap = fabsf(__fsub_rn(nb, x.hi));
+    const float u = __fmul_rn(__uint2float_rn(mix32(key) >> 8), 0x1p-24f);  // uniform in [0, 1)
+    return fabsf(x.lo) > __fmul_rn(u, gap) ? nb : x.hi;
+}
+
 template <class T>
 SMRT_D T rcp_tau(T A, T B, T rho) {
     return rho * rcp(fma(B, rho, A));
 }
+
+// Moments of the unit Maxwellian (rho = 1, u = 0, theta = 1), which the weights reproduce up to
+// the set's degree: sum_i w_i xi_i^g = prod_k (g_k - 1)!! for even g_k, 0 otherwise.
+constexpr double unit_moment3(int a, int b, int c) {
+    return ((a & 1) || (b & 1) || (c & 1)) ? 0.0 : cdfact(a - 1) * cdfact(b - 1) * cdfact(c - 1);
+}
+constexpr double unit_moment(int g) { return unit_moment3(mi_comp(g, 0), mi_comp(g, 1), mi_comp(g, 2)); }
 
 // Unnormalised Walsh-Hadamard transform of NB = 1, 2 or 4 values in place:
 // x_out[c] = sum_b (-1)^popcount(b & c) x_in[b].
@@ -258,6 +392,43 @@ struct Collide {
                 }
             });
         });
+    }
+
+    // Split precision, a2 + a3: the raw moments R_gamma = sum_i df_i e_i^gamma, |gamma| <= Nm,
+    // exactly, in fixed point (get(ic<i>) gives population i in fixed point), per sign orbit as
+    // raw_moments_of does, with the pair sums and transforms taken on 64-bit integers and the
+    // products by a^gamma accumulated in two parts (SplitAcc).
+    template <int Nm, class Get>
+    SMRT_D static void fixed_moments(Get &&get, long long (&R)[nmom(Nm)]) {
+        constexpr int Mm = nmom(Nm);
+        SplitAcc acc[Mm];
+        acc[0].add(get(ic<0>{}));
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            long long S[np], D[np];
+            static_for<np>([&](auto B) {
+                constexpr int b = decltype(B)::value, p = kOrb.pair[o][b];
+                constexpr bool fl = kOrb.flip[o][b] != 0;
+                const long long fp = get(ic<2 * p + 1>{}), fm = get(ic<2 * p + 2>{});
+                S[b] = fp + fm;
+                D[b] = fl ? fm - fp : fp - fm;
+            });
+            wht<np>(S);
+            wht<np>(D);
+            static_for<Mm>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr int m = kOrb.monomial(o, g);
+                if constexpr (m != 0) {
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        acc[g].template madd<m>(S[cl]);
+                    else
+                        acc[g].template madd<m>(D[cl]);
+                }
+            });
+        });
+        static_for<Mm>([&](auto G) { R[decltype(G)::value] = acc[decltype(G)::value].value(); });
     }
 
     // a3: ta_alpha = a_alpha / alpha! = sum_gamma hdiv(alpha, gamma) c^|gamma| R_gamma.
@@ -425,11 +596,17 @@ struct Collide {
 
     // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
     // Returns false when rho or theta is not positive (or NaN).
-    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const double (&wpd)[NP + 1], T c,
-                               double cd, const T *tauA, const T *tauB, unsigned key = 0u) {
+    SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const float (&wlo)[NP + 1], T c,
+                               float clo, const T *tauA, const T *tauB, unsigned key = 0u) {
         if constexpr (Split) {
-            return collide_split([&](auto I) { return widen<Acc>(f[decltype(I)::value]); },
-                                 [&](int i, T v) { f[i] = v; }, wp, wpd, c, cd, tauA, tauB, key);
+            bool finite = true;
+            const bool ok = collide_split(
+                [&](auto I) {
+                    finite &= (__float_as_uint(f[decltype(I)::value]) & 0x7f800000u) != 0x7f800000u;
+                    return to_fixed(f[decltype(I)::value]);
+                },
+                [&](int i, T v) { f[i] = v; }, wp, wlo, c, clo, tauA, tauB, key);
+            return ok && finite;
         } else {
             // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
             T v[M], Rc[M];
@@ -455,70 +632,231 @@ struct Collide {
         }
     }
 
-    // Split precision (T float, Acc double): pull(ic<i>) = pulled population i in Acc (exact
-    // end-state values at ghost slots), read once; store(i, value) receives post-collision
-    // population i, rounded stochastically to T, as soon as it is formed (no array of either
-    // is held, which keeps the live registers down).
-    // In Acc: the raw moments, the conserved moments, the absolute coefficients and the
-    // equilibrium they are reduced by, and the rebuild of the equilibrium with the weights and c
-    // in Acc; in T: the non-equilibrium remainder through a4-a6 and its rebuild.
+    // Split precision (T float): pullq(ic<i>) gives pulled population i in fixed point (the stored
+    // float exactly, or the exact double end-state value beyond a fixed end), read once;
+    // store(i, value) receives post-collision population i as soon as it is formed.
+    //
+    // Precision design. Float arithmetic is used only for the non-equilibrium part, whose own
+    // size then bounds its rounding errors; whatever the equilibrium carries is formed to about
+    // 2^-44 of its size, so that an equilibrium state is reproduced with no float rounding that
+    // would freeze (a steady bias in the stress or heat flux of an equilibrium far field shifts
+    // its state through the flux balance and lets a shock drift):
+    //  * raw moments R_gamma, |gamma| <= N, exactly in 64-bit fixed point;
+    //  * in two-float arithmetic: rho, u, theta from them; the equilibrium's raw moments
+    //    (Maxwellian moments, which the order-N equilibrium matches for |gamma| <= N); the
+    //    non-equilibrium raw moments R - R^eq, then rounded to float;
+    //  * in float: absolute coefficients of the non-equilibrium part and a4-a6 (to the local
+    //    frame, relaxation, back);
+    //  * in two-float: the order-N equilibrium's coefficients plus the relaxed non-equilibrium
+    //    ones, their monomial coefficients Q_g (f'_i = w_i sum_g Q_g xi_i^g), and an exact
+    //    restoration of mass, momentum and energy on them;
+    //  * the polynomial at each population in fixed point (per sign orbit), times w_i in
+    //    two-float, rounded to float stochastically.
+    // Conservation: with the quadrature moments M_g = sum_i w_i xi_i^g (the unit Maxwellian's,
+    // prod_k (g_k - 1)!! for even g, exact to the set's degree), the rebuilt populations carry
+    // mass sum_g Q_g M_g, momentum sum_g Q_g M_(g+e_k) and energy sum_g Q_g sum_k M_(g+2e_k).
+    // Whatever float rounding left in them is removed along w_i (A + B.xi_i + C (|xi_i|^2 - 3))
+    // (sum w = 1, sum w xi xi = delta, sum w |xi|^4 = 15), i.e. added to Q_0, Q_k and Q_kk, so
+    // that they equal the pre-collision sums. The stored values then conserve rho, rho u and
+    // energy in expectation, stochastic rounding being the only remaining error.
     template <class Pull, class Store>
-    SMRT_D static bool collide_split(Pull &&pull, Store &&store, const T (&wp)[NP + 1],
-                                     const double (&wpd)[NP + 1], T c, double cd, const T *tauA,
+    SMRT_D static bool collide_split(Pull &&pullq, Store &&store, const T (&wp)[NP + 1],
+                                     const float (&wlo)[NP + 1], T c, float clo, const T *tauA,
                                      const T *tauB, unsigned key) {
-        Acc Ra[M], va[M], teq[M], raw[5];
-        raw_moments_of<N>(pull, Ra);
-        raw[0] = Ra[0];
-        raw[1] = Ra[mi_pos(1, 0, 0)];
-        raw[2] = Ra[mi_pos(0, 1, 0)];
-        raw[3] = Ra[mi_pos(0, 0, 1)];
-        raw[4] = Ra[mi_pos(2, 0, 0)] + Ra[mi_pos(0, 2, 0)] + Ra[mi_pos(0, 0, 2)];
-        Acc rho_a, rhom1_a, u_a[3], th_a, thm1_a;
-        from_raw_sums(raw, Acc(cd), rho_a, rhom1_a, u_a, th_a, thm1_a);
-        scaled_to_absolute<N>(Acc(cd), va, Ra);
-        equilibrium<Acc>(rho_a, rhom1_a, u_a, thm1_a, teq);
-        // the non-equilibrium remainder a - a^eq (d^eq = (rho, 0, ...) in the local frame, so
-        // d_n = [T^-1 (a - a^eq)]_n for n >= 2); slot 0 carries nothing of it
+        static_assert(std::is_same<T, float>::value, "the split precision stores floats");
+        constexpr int px = mi_pos(1, 0, 0), py = mi_pos(0, 1, 0), pz = mi_pos(0, 0, 1);
+        constexpr int pxx = mi_pos(2, 0, 0), pyy = mi_pos(0, 2, 0), pzz = mi_pos(0, 0, 2);
+        // a2 + a3: exact raw moments; rho, u, theta in two-float
+        long long Rq[M];
+        fixed_moments<N>(pullq, Rq);
+        const ff cc = {c, clo};
+        ff cp[N + 1];  // c^j
+        cp[0] = ff{1.f, 0.f};
+        static_for<N>([&](auto J) { cp[decltype(J)::value + 1] = cp[decltype(J)::value] * cc; });
+        const ff r = fixed_to_ff(Rq[0]);  // rho - 1
+        const ff rho = r + 1.f;
+        const ff irho = ff_div(ff{1.f, 0.f}, rho);
+        const ff mom[3] = {cc * fixed_to_ff(Rq[px]), cc * fixed_to_ff(Rq[py]), cc * fixed_to_ff(Rq[pz])};
+        const ff uf[3] = {mom[0] * irho, mom[1] * irho, mom[2] * irho};
+        const ff en = cp[2] * fixed_to_ff(Rq[pxx] + Rq[pyy] + Rq[pzz]);  // E - 3
+        // theta - 1 = (E - 3 - 3 (rho - 1) - rho |u|^2) / (3 rho)
+        const ff thm1 = (en - r * 3.f - (mom[0] * uf[0] + mom[1] * uf[1] + mom[2] * uf[2])) *
+                        (ff_inv<3>() * irho);
+        const ff theta = thm1 + 1.f;
+        // non-equilibrium raw moments in xi-units, c^|g| R_g - (rho prod_k mu_{g_k}(u_k, theta)
+        // - prod_k mu_{g_k}(0, 1)), mu_j the raw moments of a 1D Gaussian of mean u and variance
+        // theta (mu_{j+1} = u mu_j + j theta mu_{j-1}); orders 0 and 1 vanish by definition of
+        // rho and u
         T v[M];
-        v[0] = T(0);
-        static_for<M - 1>([&](auto A) {
-            constexpr int p = decltype(A)::value + 1;
-            v[p] = T(va[p] - teq[p]);
+        {
+            ff mu[3][N + 1];
+            static_for<3>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                mu[k][0] = ff{1.f, 0.f};
+                mu[k][1] = uf[k];
+                static_for<N - 1>([&](auto J) {
+                    constexpr int j = decltype(J)::value + 1;
+                    mu[k][j + 1] = uf[k] * mu[k][j] + theta * mu[k][j - 1] * float(j);
+                });
+            });
+            T Rx[M];
+            static_for<M>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                if constexpr (mi_order(g) <= 1) {
+                    Rx[g] = T(0);
+                } else {
+                    constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+                    ff eq = rho;
+                    if constexpr (g0 > 0) eq = eq * mu[0][g0];
+                    if constexpr (g1 > 0) eq = eq * mu[1][g1];
+                    if constexpr (g2 > 0) eq = eq * mu[2][g2];
+                    Rx[g] = (fixed_to_ff(Rq[g]) * cp[mi_order(g)] - (eq + float(-unit_moment(g)))).hi;
+                }
+            });
+            // a3 on the non-equilibrium part: divided absolute coefficients (float)
+            static_for<M>([&](auto A) {
+                constexpr int al = decltype(A)::value;
+                T acc = T(0);
+                static_for<M>([&](auto G) {
+                    constexpr int g = decltype(G)::value;
+                    constexpr double h = hdiv(al, g);
+                    if constexpr (h != 0.0 && mi_order(g) >= 2) acc = fma(T(h), Rx[g], acc);
+                });
+                v[al] = acc;
+            });
+        }
+        const T rhof = rho.hi, thm1f = thm1.hi, thetaf = theta.hi;
+        const T u[3] = {uf[0].hi, uf[1].hi, uf[2].hi};
+        const bool ok = (rhof > T(0)) && (thetaf > T(0));
+        // a4-a6 on the non-equilibrium part; orders 0 and 1 leave as zero
+        relax_coefficients(v, u, rhof, thetaf, thm1f, T(0), tauA, tauB);
+        // the post-collision coefficients: order-N equilibrium ta^eq_alpha = rho prod_k
+        // G_k[alpha_k] (slot 0: rho - 1; G_k[j+1] = (u_k G_k[j] + (theta - 1) G_k[j-1]) / (j + 1))
+        // plus the relaxed non-equilibrium part, then the monomial coefficients in xi,
+        // Q_g = sum_alpha hfull(alpha, g) ta_alpha (integers hfull)
+        ff Qx[M];
+        {
+            ff G[3][N + 1];
+            static_for<3>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                G[k][0] = ff{1.f, 0.f};
+                G[k][1] = uf[k];
+                static_for<N - 1>([&](auto J) {
+                    constexpr int j = decltype(J)::value + 1;
+                    G[k][j + 1] = (uf[k] * G[k][j] + thm1 * G[k][j - 1]) * ff_inv<j + 1>();
+                });
+            });
+            ff ta[M];
+            static_for<M>([&](auto A) {
+                constexpr int al = decltype(A)::value;
+                constexpr int a0 = mi_comp(al, 0), a1 = mi_comp(al, 1), a2 = mi_comp(al, 2);
+                if constexpr (al == 0) {
+                    ta[al] = r;
+                } else {
+                    ff t = rho;
+                    if constexpr (a0 > 0) t = t * G[0][a0];
+                    if constexpr (a1 > 0) t = t * G[1][a1];
+                    if constexpr (a2 > 0) t = t * G[2][a2];
+                    ta[al] = mi_order(al) >= 2 ? t + v[al] : t;
+                }
+            });
+            static_for<M>([&](auto G_) {
+                constexpr int g = decltype(G_)::value;
+                ff acc = ff{0.f, 0.f};
+                static_for<M>([&](auto A) {
+                    constexpr int al = decltype(A)::value;
+                    constexpr double h = hfull(al, g);
+                    if constexpr (h == 1.0)
+                        acc = acc + ta[al];
+                    else if constexpr (h != 0.0)
+                        acc = acc + ta[al] * float(h);
+                });
+                Qx[g] = acc;
+            });
+        }
+        // exact restoration of mass, momentum and energy (targets: rho - 1, rho u, E - 3)
+        {
+            ff ms = ff{0.f, 0.f}, es = ff{0.f, 0.f}, js[3] = {ff{0.f, 0.f}, ff{0.f, 0.f}, ff{0.f, 0.f}};
+            static_for<M>([&](auto G_) {
+                constexpr int g = decltype(G_)::value;
+                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+                constexpr double m0 = unit_moment(g);
+                constexpr double e0 = unit_moment3(g0 + 2, g1, g2) + unit_moment3(g0, g1 + 2, g2) +
+                                      unit_moment3(g0, g1, g2 + 2);
+                if constexpr (m0 != 0.0) ms = ms + (m0 == 1.0 ? Qx[g] : Qx[g] * float(m0));
+                if constexpr (e0 != 0.0) es = es + Qx[g] * float(e0);
+                static_for<3>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    constexpr double j0 = unit_moment3(g0 + (k == 0), g1 + (k == 1), g2 + (k == 2));
+                    if constexpr (j0 != 0.0) js[k] = js[k] + (j0 == 1.0 ? Qx[g] : Qx[g] * float(j0));
+                });
+            });
+            const ff A = r - ms;
+            const ff Cc = (en - es - A * 3.f) * ff_inv<6>();
+            Qx[0] = Qx[0] + (A - Cc * 3.f);
+            Qx[px] = Qx[px] + (mom[0] - js[0]);
+            Qx[py] = Qx[py] + (mom[1] - js[1]);
+            Qx[pz] = Qx[pz] + (mom[2] - js[2]);
+            Qx[pxx] = Qx[pxx] + Cc;
+            Qx[pyy] = Qx[pyy] + Cc;
+            Qx[pzz] = Qx[pzz] + Cc;
+        }
+        // monomial coefficients in e (xi = c e), in fixed point
+        long long Pq[M];
+        static_for<M>([&](auto G_) {
+            constexpr int g = decltype(G_)::value;
+            const ff P = mi_order(g) > 0 ? Qx[g] * cp[mi_order(g)] : Qx[g];
+            Pq[g] = to_fixed<kFixP>(P.hi) + to_fixed<kFixP>(P.lo);
         });
-        const bool ok = (rho_a > Acc(0)) && (th_a > Acc(0));
-        const T rho = T(rho_a), theta = T(th_a), thm1 = T(thm1_a);
-        const T u[3] = {T(u_a[0]), T(u_a[1]), T(u_a[2])};
-        relax_coefficients(v, u, rho, theta, thm1, T(0), tauA, tauB);
-        T oneq[Q];
-        rebuild<T>(v, c, wp, oneq);
-        // Conservation in Acc. The equilibrium rebuilt in Acc carries the pre-collision rho, rho u
-        // and E (the quadrature is exact for them), while the float remainder, zero in those
-        // moments in exact arithmetic, carries rounding errors that freeze once the flow is
-        // steady and would drift them. Its sums, exact in Acc, are removed along the conserved
-        // directions d_i = w_i (A + B.e_i + C (|e_i|^2 - 3/c^2)) (sum w = 1, sum w e e = 1/c^2,
-        // sum w |e|^2 = 3/c^2, sum w |e|^4 = 15/c^4), folded into the equilibrium's coefficients.
-        Acc m[5];
-        conserved_sums(oneq, m);
-        const Acc c2 = Acc(cd) * Acc(cd);
-        const Acc A = -m[0];
-        const Acc C = c2 * c2 * (-m[4] - Acc(3) * A / c2) / Acc(6);
-        const Acc corr[5] = {A - C * Acc(3) / c2, -c2 * m[1], -c2 * m[2], -c2 * m[3], C};
-        rebuild_emit(teq, Acc(cd), wpd, [&](int i, Acc v) {
-            store(i, round_stochastic(v + widen<Acc>(oneq[i]), key ^ (0x9e3779b9u * unsigned(i + 1))));
-        }, corr);
+        // a7 + a8: f'_i = w_i P(e_i), P(e_i) per sign orbit in fixed point (sums per parity
+        // class, Walsh-Hadamard transform), then times w_i in two-float, rounded stochastically
+        auto out = [&](int i, int wi, long long poly) {
+            const ff w = {wp[wi], wlo[wi]};
+            store(i, round_stochastic(w * fixed_to_ff<kFixP>(poly), key ^ (0x9e3779b9u * unsigned(i + 1))));
+        };
+        out(0, 0, Pq[0]);
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            SplitAcc Ea[np], Oa[np];
+            static_for<M>([&](auto G_) {
+                constexpr int g = decltype(G_)::value;
+                constexpr int m = kOrb.monomial(o, g);
+                if constexpr (m != 0) {
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        Ea[cl].template madd<m>(Pq[g]);
+                    else
+                        Oa[cl].template madd<m>(Pq[g]);
+                }
+            });
+            long long E[np], Od[np];
+            static_for<np>([&](auto B) {
+                E[decltype(B)::value] = Ea[decltype(B)::value].value();
+                Od[decltype(B)::value] = Oa[decltype(B)::value].value();
+            });
+            wht<np>(E);
+            wht<np>(Od);
+            static_for<np>([&](auto B) {
+                constexpr int b = decltype(B)::value, p = kOrb.pair[o][b];
+                constexpr bool fl = kOrb.flip[o][b] != 0;
+                out(fl ? 2 * p + 2 : 2 * p + 1, p + 1, E[b] + Od[b]);
+                out(fl ? 2 * p + 1 : 2 * p + 2, p + 1, E[b] - Od[b]);
+            });
+        });
         return ok;
     }
 };
 
 // ------------------------------------------------------------------------------ loaders
 // Blocks of 128 threads per SM that the step kernels leave room for (0: no minimum, the
-// compiler's own register choice). The split-precision collision keeps more values live than
-// fit in 255 registers at useful occupancy (two warps per scheduler wait on their own
-// double-precision results); capped at 128 registers (four such blocks) it spills part of them
-// to L1 and runs the batched D3Q103 shocks 18 % faster. An explicit minimum of 1 would instead
-// let the float box kernel grow from 64 to 128 registers and halve its occupancy.
+// compiler's own register choice). The split-precision collision would take all 255 registers
+// at two blocks per SM; capped at 168 (three blocks) it spills a few hundred bytes to L1 and runs
+// the batched D3Q103 shocks 1.4x faster (0.60 -> 0.44 ms per step; 128 registers gives the
+// same). An explicit minimum of 1 would instead let the float box kernel grow from 64 to 128
+// registers and halve its occupancy.
 template <bool Split>
-constexpr int kStepMinBlocks = Split ? 4 : 0;
+constexpr int kStepMinBlocks = Split ? 3 : 0;
 
 SMRT_HD int wrap(int t, int n) { return t < 0 ? t + n : (t >= n ? t - n : t); }
 
@@ -544,7 +882,7 @@ __global__ void __launch_bounds__(128, kStepMinBlocks<Split>) step_box_kernel(St
             f[i] = a.fin[a.plane[i] + zs * slab + ys * row + xs];
         });
     });
-    const bool ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]),
+    const bool ok = C::collide(f, a.wp, a.wlo, a.c, a.clo, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]),
                                mix32(unsigned(z * slab + y * row + x) ^ mix32(a.step)));
     if (!ok) atomicOr(a.health, 1u);
     const long long cell = z * slab + y * row + x;
@@ -581,21 +919,27 @@ SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *_
     const double *gld = a.ghostsd + (long long)tile.x * 2 * Lat::Q;
     const double *grd = gld + Lat::Q;
     // pull of population i from cell xs of the instance: the stored state inside, the end
-    // states beyond a fixed end (in double for the split precision, exact)
-    using V = typename std::conditional<Split, Acc, T>::type;
-    auto pull = [&](int i, int xs) -> V {
+    // states beyond a fixed end
+    auto pull = [&](int i, int xs) -> T {
         if constexpr (FixedX) {
-            if constexpr (Split) {
-                if (xs < 0) return V(gld[i]);
-                if (xs >= L) return V(grd[i]);
-            } else {
-                if (xs < 0) return gl[i];
-                if (xs >= L) return gr[i];
-            }
-            return widen<V>(load_pop<Coherent>(fin + a.plane[i] + base + xs));
+            if (xs < 0) return gl[i];
+            if (xs >= L) return gr[i];
+            return load_pop<Coherent>(fin + a.plane[i] + base + xs);
         } else {
-            return widen<V>(load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L)));
+            return load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L));
         }
+    };
+    // ... for the split precision, in fixed point (the exact double end state beyond a fixed
+    // end); a non-finite stored value is recorded
+    bool finite = true;
+    auto pull_split = [&](int i, int xs) -> long long {
+        if constexpr (FixedX) {
+            if (xs < 0) return to_fixed(gld[i]);
+            if (xs >= L) return to_fixed(grd[i]);
+        }
+        const float v = float(pull(i, xs));
+        finite &= (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+        return to_fixed(v);
     };
     // x-distance of population i's pull: the rest population streams by k as well
     auto src_x = [&](auto I) {
@@ -605,13 +949,14 @@ SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *_
     };
     bool ok;
     if constexpr (Split) {
-        ok = C::collide_split([&](auto I) { return pull(decltype(I)::value, src_x(I)); },
-                              [&](int i, T v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wpd, a.c,
-                              a.cd, tau_a<T>(in), tau_b<T>(in), mix32(unsigned(base + x) ^ mix32(step)));
+        ok = C::collide_split([&](auto I) { return pull_split(decltype(I)::value, src_x(I)); },
+                              [&](int i, T v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wlo, a.c,
+                              a.clo, tau_a<T>(in), tau_b<T>(in), mix32(unsigned(base + x) ^ mix32(step)));
+        ok = ok && finite;
     } else {
         T f[Lat::Q];
         static_for<Lat::Q>([&](auto I) { f[decltype(I)::value] = pull(decltype(I)::value, src_x(I)); });
-        ok = C::collide(f, a.wp, a.wpd, a.c, a.cd, tau_a<T>(in), tau_b<T>(in),
+        ok = C::collide(f, a.wp, a.wlo, a.c, a.clo, tau_a<T>(in), tau_b<T>(in),
                         mix32(unsigned(base + x) ^ mix32(step)));
         static_for<Lat::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
