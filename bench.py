@@ -248,8 +248,9 @@ print(json.dumps({{"rate": {L} * lat.q * {steps} / dt, "seconds": dt}}))
 
 def run_batched(args, world: int, rank: int, local: int) -> None:
     """64 independent 1D shocks (Ma ~ U[1.2, 3], lengths from {512..8192}, seed 11086), D3Q103,
-    N = 4, FP32 populations with FP64 conserved sums, autotuned launch schedule. With N ranks
-    the instances are split between them (no data exchange: the problems are independent)."""
+    N = 4, FP32 populations with exact fixed-point conserved sums and a two-float equilibrium,
+    autotuned launch schedule. With N ranks the instances are split between them (no data
+    exchange: the problems are independent)."""
     import numpy as np
     import torch
 
@@ -305,7 +306,9 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
     achieved = 2.0 * q * 4 * cells * K / (ms * 1e-3) / 1e9
     # the FP64 pipe bounds this kernel: its double-precision operations per cell-step (ncu
     # instruction counts, an FMA counted as two) against the nominal FP64 rate
-    gflop = BATCHED_FP64_FLOP_PER_CELL * cells * K / (ms * 1e-3) / 1e9
+    # the kernel is bound by instruction issue (ncu: 26 % issue-active, instruction-fetch stalls
+    # first): its warp instructions per cell-step against one per clock per scheduler
+    ginst = BATCHED_WARP_INST_PER_CELL * cells * K / (ms * 1e-3) / 1e9
     if rank != 0:
         return
     cpu = None
@@ -315,17 +318,19 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
                "sample": "one Ma = 3 shock of 512 cells (D3Q103, N = 4), 40 FP64 oracle steps"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (f64 conserved sums and equilibrium)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 (exact fixed-point moments and conserved sums, two-float equilibrium)", "data": "synthetic",
             "config": {"workload": "batched_shocks_64_d3q103_n4", "instances_per_gpu": int(len(machs)),
                        "cells_per_gpu": cells, "velocities": q, "hermite_order": 4,
                        "schedule": sched,
                        "l2": "L2 flushed (256 MB write) before every timed step; steps timed one by one"},
-            "roofline": {"bound": "alu", "achieved": gflop, "peak": FP64_PEAK_GFLOPS,
-                         "unit": "GFLOP/s (fp64)", "frac": gflop / FP64_PEAK_GFLOPS,
+            "roofline": {"bound": "alu", "achieved": ginst, "peak": ISSUE_PEAK_GINST,
+                         "unit": "G warp-instructions/s", "frac": ginst / ISSUE_PEAK_GINST,
                          "traffic": profile_value(PROFILE_BATCHED, "dram_bytes_per_launch"),
-                         "peak_kind": "nominal FP64 rate", "flop_per_cell": BATCHED_FP64_FLOP_PER_CELL,
+                         "peak_kind": "instruction issue: 4 schedulers x 152 SMs x 2070 MHz, one warp "
+                                      "instruction per clock each",
+                         "warp_inst_per_cell": BATCHED_WARP_INST_PER_CELL,
                          "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak,
-                         "note": "double-precision arithmetic, not HBM, limits this workload"},
+                         "note": "instruction issue (fetch-bound), not HBM, limits this workload"},
             "cpu_baseline": cpu, "gpu_launches": K,
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -336,8 +341,11 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
 # nominal FP64 rate of a GB300
 TP_FP64_FLOP_PER_CELL = 14949.0
 FP64_PEAK_GFLOPS = 1250.0
-# the same for the split-precision D3Q103, N = 4 line kernel on the 64 batched shocks
-BATCHED_FP64_FLOP_PER_CELL = 2691.0
+# warp instructions per cell-step of the split-precision D3Q103, N = 4 staged line kernel on the
+# 64 batched shocks (ncu smsp__inst_executed.sum of one launch / cells), and the issue rate of a
+# GB300 (4 schedulers per SM, 152 SMs, 2070 MHz, one warp instruction per clock each)
+BATCHED_WARP_INST_PER_CELL = 501.9
+ISSUE_PEAK_GINST = 4 * 152 * 2.07
 
 
 def table3_instances(rank: int, count: int = 512, length: int = 0):

@@ -125,7 +125,11 @@ lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lattice, const lb
  *      s = 1 when it is 0. Every tau must be > 0.
  * left, right: end states of a grid with bc_x = 1 (host memory; may be NULL when bc_x = 0).
  * instance: which instance of a batch to set (-1 = all).
- * Enqueues the computation of the end-state populations on the context's stream.
+ * Validates and stores the settings on the host. The instance table and the end-state
+ * populations of every instance set since the last launch are uploaded and computed, in one
+ * launch, on the context's stream by the next call that launches work (lb_fill_equilibrium,
+ * lb_step, lb_step_graph, lb_autotune, lb_moments, the adjoint calls), which then synchronises
+ * once; setting many instances one by one therefore costs one launch.
  * Errors: LB_ERR_INVALID (null, tau <= 0, rho or theta <= 0, bad instance), LB_ERR_CUDA. */
 lb_status lb_set_relaxation(lb_ctx *ctx, const double *tau, int maxwell_molecule_law,
                             double rho_ref, const lb_state *left, const lb_state *right,
@@ -133,7 +137,9 @@ lb_status lb_set_relaxation(lb_ctx *ctx, const double *tau, int maxwell_molecule
 
 /* lb_set_frame_shift -- change the integer frame shift k_x of one instance (-1 = all) after
  * lb_init_lattice (Sec. 4.1: each shock chooses k_x = round(((u1 + u2)/2) / c)). Call before
- * lb_set_relaxation so that the end-state populations use the new frame. Synchronises.
+ * lb_set_relaxation so that the end-state populations use the new frame (end states already set
+ * are recomputed in the new frame). Stored on the host and uploaded as lb_set_relaxation's
+ * settings are.
  * Errors: LB_ERR_INVALID (bad instance; a single box accepts only -1), LB_ERR_CUDA. */
 lb_status lb_set_frame_shift(lb_ctx *ctx, int instance, int kx);
 
@@ -149,7 +155,8 @@ lb_status lb_set_frame_shift(lb_ctx *ctx, int instance, int kx);
  * toward the coefficients of that Gaussian, truncated at N. The discrete scheme uses
  * b' = 1 - (1 - b) tau_20 / (tau_20 - b/2), which keeps the continuous model's stress rate
  * (1 - b)/tau_c under the second-order discretisation, so Pr = 1/(1 - b) (2/3 at b = -1/2).
- * Requires -1/2 <= b < 1. Tensor-product sets (D3Q729, D3Q4913) only. Synchronises.
+ * Requires -1/2 <= b < 1. Tensor-product sets (D3Q729, D3Q4913) only. Stored on the host and
+ * uploaded as lb_set_relaxation's settings are.
  * Errors: LB_ERR_INVALID (instance, model or b), LB_ERR_UNSUPPORTED (other sets), LB_ERR_CUDA. */
 lb_status lb_set_collision_model(lb_ctx *ctx, int instance, int model, double b);
 
@@ -253,9 +260,14 @@ lb_status lb_step_adjoint(lb_ctx *ctx, const void *f_t, const double *lam_next, 
  * device-memory budget. The paper has no counterpart; the arguments, results and errors are
  * those of lb_step_adjoint, and the call allocates nothing. Instead of the context's scratch
  * it uses one fixed array of 8192 x 10 doubles (640 KB) that every GPU loading libsmrt holds
- * until the process exits, enough for grids of up to 8192 blocks of 128 cells (1,048,576
- * cells); larger grids return LB_ERR_INVALID. The first call on a device looks up that
- * array's device address: make that first call before any stream capture. All calls share
+ * until the process exits, enough for grids of up to 8192 blocks: a box of up to 8192 blocks
+ * of 128 cells along x (1,048,576 cells), or batched lines of up to 8192 tiles of the
+ * scheduled tile width (lb_set_schedule: 32, 64 or 128 cells per tile, so at most 262,144
+ * cells at width 32 and 1,048,576 at width 128); larger grids return LB_ERR_INVALID and
+ * touch neither lam_t nor dtau. The first call on a device looks up that array's device
+ * address, and settings changed since the context's last launch (lb_set_relaxation and its
+ * kin) are uploaded first with a synchronising copy: make the first call, and a launching call
+ * after any change of settings, before any stream capture. All calls share
  * the array and it keeps the last call's partial sums (each call overwrites the slots it reads,
  * so nothing needs clearing), hence calls that may overlap on the GPU -- on different streams
  * or contexts of one device -- race and must be ordered by the caller. */

@@ -45,6 +45,10 @@ struct lb_ctx {
     std::vector<InstanceInfo> h_inst;
     std::vector<double> h_states;  // [instance][side][rho, ux, uy, uz, theta]
     bool relax_set;
+    // settings not yet on the device: the instance table, and the end states of instances
+    // [ghost_lo, ghost_hi) (flush_tables uploads them before the next launch)
+    bool tables_dirty;
+    int ghost_lo, ghost_hi;
     // device tables owned by the context
     InstanceInfo *d_inst;
     int2 *d_tiles;
@@ -360,9 +364,53 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     v.health = c->d_health;
     v.bar = c->d_health + 1;
     c->relax_set = false;
+    c->tables_dirty = false;
+    c->ghost_lo = grid->batch;
+    c->ghost_hi = 0;
     *out = c;
     return LB_OK;
 }
+
+namespace {
+
+// Upload what lb_set_relaxation, lb_set_frame_shift and lb_set_collision_model changed since the
+// last launch: the instance table, then the end-state populations of the instances whose end
+// states or frame changed, in one launch over their range; synchronises once (the host tables
+// are reused by the next setting).
+lb_status flush_tables(lb_ctx *c) {
+    if (!c->tables_dirty) return LB_OK;
+    cudaStream_t st = c->view.stream;
+    cudaError_t e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * c->batch,
+                                    cudaMemcpyHostToDevice, st);
+    const int j0 = c->ghost_lo, j1 = c->ghost_hi;
+    if (e == cudaSuccess && c->view.fixedx && j0 < j1) {
+        e = cudaMemcpyAsync(c->d_states, c->h_states.data(), sizeof(double) * 10 * c->batch, cudaMemcpyHostToDevice,
+                            st);
+        if (e == cudaSuccess) {
+            // a view whose instance table starts at j0
+            CtxView gv = c->view;
+            gv.inst = c->d_inst + j0;
+            e = c->ks->ghost(gv, c->d_states + 10 * (size_t)j0, j1 - j0,
+                             static_cast<char *>(c->d_ghosts) + c->elem * c->q * 2 * (size_t)j0,
+                             c->d_ghostsd + (size_t)c->q * 2 * j0);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return LB_ERR_CUDA;
+    c->tables_dirty = false;
+    c->ghost_lo = c->batch;
+    c->ghost_hi = 0;
+    return LB_OK;
+}
+
+void mark_ghosts(lb_ctx *c, int j0, int j1) {
+    c->tables_dirty = true;
+    if (!c->view.fixedx) return;
+    c->ghost_lo = std::min(c->ghost_lo, j0);
+    c->ghost_hi = std::max(c->ghost_hi, j1);
+}
+
+}  // namespace
 
 extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell, double rho_ref,
                                        const lb_state *left, const lb_state *right, int instance) {
@@ -403,24 +451,7 @@ extern "C" lb_status lb_set_relaxation(lb_ctx *c, const double *tau, int maxwell
             }
         }
     }
-    cudaStream_t st = c->view.stream;
-    cudaError_t e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * c->batch,
-                                    cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && c->view.fixedx) {
-        e = cudaMemcpyAsync(c->d_states, c->h_states.data(), sizeof(double) * 10 * c->batch,
-                            cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) {
-            // end-state populations of the instances just set only (a view whose instance
-            // table starts at j0)
-            CtxView gv = c->view;
-            gv.inst = c->d_inst + j0;
-            e = c->ks->ghost(gv, c->d_states + 10 * (size_t)j0, j1 - j0,
-                             static_cast<char *>(c->d_ghosts) + c->elem * c->q * 2 * (size_t)j0,
-                             c->d_ghostsd + (size_t)c->q * 2 * j0);
-        }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables are reused next call
-    if (e != cudaSuccess) return LB_ERR_CUDA;
+    mark_ghosts(c, j0, j1);
     c->relax_set = true;
     return LB_OK;
 }
@@ -431,10 +462,11 @@ extern "C" lb_status lb_set_frame_shift(lb_ctx *c, int instance, int kx) {
     const int j0 = instance < 0 ? 0 : instance, j1 = instance < 0 ? c->batch : instance + 1;
     for (int j = j0; j < j1; ++j) c->h_inst[j].kx = kx;
     if (!c->view.line) c->view.kx = kx;
-    cudaError_t e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * c->batch,
-                                    cudaMemcpyHostToDevice, c->view.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
-    return cuda_status(e);
+    if (c->relax_set)
+        mark_ghosts(c, j0, j1);  // end states already set are rebuilt in the new frame
+    else
+        c->tables_dirty = true;
+    return LB_OK;
 }
 
 extern "C" lb_status lb_set_collision_model(lb_ctx *c, int instance, int model, double b) {
@@ -447,15 +479,15 @@ extern "C" lb_status lb_set_collision_model(lb_ctx *c, int instance, int model, 
         c->h_inst[j].model = model;
         c->h_inst[j].es_b = model == LB_MODEL_ES_BGK ? b : 0.0;
     }
-    cudaError_t e = cudaMemcpyAsync(c->d_inst, c->h_inst.data(), sizeof(InstanceInfo) * c->batch,
-                                    cudaMemcpyHostToDevice, c->view.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
-    return cuda_status(e);
+    c->tables_dirty = true;
+    return LB_OK;
 }
 
 extern "C" lb_status lb_fill_equilibrium(lb_ctx *c, void *f, const double *rho, const double *u,
                                          const double *theta) {
     if (!c || !f || !rho || !u || !theta) return LB_ERR_INVALID;
+    const lb_status fs = flush_tables(c);
+    if (fs != LB_OK) return fs;
     return cuda_status(c->ks->fill(c->view, f, rho, u, theta));
 }
 
@@ -499,7 +531,8 @@ cudaError_t launch_persistent(lb_ctx *c, const CtxView &v, void *fa, void *fb, i
 }  // namespace
 
 extern "C" lb_status lb_step(lb_ctx *c, void *fa, void *fb, int nsteps) {
-    const lb_status st = check_pair(c, fa, fb, nsteps);
+    lb_status st = check_pair(c, fa, fb, nsteps);
+    if (st == LB_OK) st = flush_tables(c);
     if (st != LB_OK) return st;
     if (c->view.line && c->sched.persistent) return cuda_status(launch_persistent(c, c->view, fa, fb, nsteps));
     void *src = fa, *dst = fb;
@@ -602,7 +635,8 @@ extern "C" lb_status lb_autotune(lb_ctx *c, void *fa, void *fb, int trial_steps,
 }
 
 extern "C" lb_status lb_test_barrier_timeout(lb_ctx *c, void *fa, void *fb) {
-    const lb_status st = check_pair(c, fa, fb, 2);
+    lb_status st = check_pair(c, fa, fb, 2);
+    if (st == LB_OK) st = flush_tables(c);
     if (st != LB_OK) return st;
     if (!c->view.line) return LB_ERR_UNSUPPORTED;
     const long long grid = persistent_grid(c);
@@ -617,7 +651,8 @@ extern "C" lb_status lb_test_barrier_timeout(lb_ctx *c, void *fa, void *fb) {
 }
 
 extern "C" lb_status lb_step_graph(lb_ctx *c, void *fa, void *fb, int nsteps) {
-    const lb_status st = check_pair(c, fa, fb, nsteps);
+    lb_status st = check_pair(c, fa, fb, nsteps);
+    if (st == LB_OK) st = flush_tables(c);
     if (st != LB_OK) return st;
     if (!c->view.line || persistent_grid(c) < 1) return LB_ERR_UNSUPPORTED;
     const bool same = c->graph && c->graph_fa == fa && c->graph_fb == fb && c->graph_steps == nsteps &&
@@ -659,6 +694,8 @@ extern "C" lb_status lb_step_graph(lb_ctx *c, void *fa, void *fb, int nsteps) {
 
 extern "C" lb_status lb_moments(lb_ctx *c, const void *f, double *out, unsigned mask) {
     if (!c || !f || !out || mask == 0 || (mask & ~0x3fu)) return LB_ERR_INVALID;
+    const lb_status fs = flush_tables(c);
+    if (fs != LB_OK) return fs;
     return cuda_status(c->ks->moments(c->view, f, out, mask));
 }
 
@@ -669,6 +706,8 @@ extern "C" lb_status lb_step_adjoint(lb_ctx *c, const void *f_t, const double *l
     const size_t bytes = sizeof(double) * lb_state_elems(c);
     const char *a0 = reinterpret_cast<const char *>(lam_next), *b0 = reinterpret_cast<const char *>(lam_t);
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;
+    const lb_status fs = flush_tables(c);
+    if (fs != LB_OK) return fs;
     return cuda_status(c->as->step(c->view, f_t, lam_next, lam_t, c->d_partials, dtau));
 }
 
@@ -676,6 +715,8 @@ extern "C" lb_status lb_moments_adjoint(lb_ctx *c, const void *f, const double *
     if (!c || !f || !gbar || !lam || mask == 0) return LB_ERR_INVALID;
     if (mask & ~(LB_MOM_RHO | LB_MOM_U | LB_MOM_THETA | LB_MOM_Q)) return LB_ERR_INVALID;
     if (!c->as) return LB_ERR_UNSUPPORTED;
+    const lb_status fs = flush_tables(c);
+    if (fs != LB_OK) return fs;
     return cuda_status(c->as->moments(c->view, f, gbar, mask, lam));
 }
 
@@ -772,7 +813,8 @@ extern "C" lb_status lb_step_adjoint_noalloc(lb_ctx *c, const void *f_t, const d
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;
     if (adj_blocks(c->view) > kNoallocMaxBlocks) return LB_ERR_INVALID;  // grid too large
     double *scratch = nullptr;
-    const lb_status st = noalloc_scratch(&scratch);
+    lb_status st = noalloc_scratch(&scratch);
+    if (st == LB_OK) st = flush_tables(c);
     if (st != LB_OK) return st;
     // every block writes its own slot before the reduction reads it: nothing to clear
     return cuda_status(c->as->step(c->view, f_t, lam_next, lam_t, scratch, dtau));

@@ -95,9 +95,83 @@ StepArgs<Lat, T> make_args(const CtxView &v, const void *fin, void *fout) {
     return a;
 }
 
+// cuTensorMapEncodeTiled, looked up through the runtime (no link-time dependence on the
+// driver library).
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+inline TensorMapEncodeFn tensor_map_encoder() {
+    static const TensorMapEncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return TensorMapEncodeFn(nullptr);
+        return reinterpret_cast<TensorMapEncodeFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a float state for the staged split-precision lines: [Q planes][stride cells],
+// box of kSeg cells x Q planes (every row a warp's pulls can reach). False when staging does not
+// apply (caller plane order differs from the library order, base or plane stride not on 16
+// bytes, coordinates beyond int32) or the driver refuses the map; the plain kernels run then.
+template <class Lat>
+bool line_staging_applies(const CtxView &v) {
+    return tensor_map_encoder() && v.plane_identity && (v.stride * 4ll) % 16 == 0 &&
+           v.stride + 2 * LineStage<Lat>::kSeg < (1ll << 31);
+}
+template <class Lat>
+bool line_encode_map(const CtxView &v, const void *state, CUtensorMap *m) {
+    const TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!line_staging_applies<Lat>(v) || !state || (reinterpret_cast<unsigned long long>(state) & 15ull) != 0ull)
+        return false;
+    const cuuint64_t dims[2] = {cuuint64_t(v.stride), cuuint64_t(Lat::Q)};
+    const cuuint64_t strides[1] = {cuuint64_t(v.stride) * 4u};
+    const cuuint32_t box[2] = {cuuint32_t(LineStage<Lat>::kSeg), cuuint32_t(Lat::Q)};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(state), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The staged kernels may take more than the default 48 KB of dynamic shared memory: raise the
+// limit of each instantiation to what a 128-thread block needs, once per device.
+template <auto Kernel, class Lat>
+cudaError_t line_smem_limit() {
+    constexpr int kDevices = 64;
+    static std::atomic<int> state[kDevices];  // 0 not set, 1 set, 2 failed
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+    if (state[dev].load(std::memory_order_acquire) == 1) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(LineStage<Lat>::persistent_bytes(128)));
+    state[dev].store(e == cudaSuccess ? 1 : 2, std::memory_order_release);
+    return e;
+}
+
 template <class Lat, int N, class T, class Acc, bool Split>
 cudaError_t launch_step(const CtxView &v, const void *fin, void *fout) {
     const StepArgs<Lat, T> a = make_args<Lat, T>(v, fin, fout);
+    if constexpr (Split) {
+        CUtensorMap map;
+        if (v.line && line_encode_map<Lat>(v, fin, &map)) {
+            const size_t smem = LineStage<Lat>::bytes(v.tile_width);
+            if (v.fixedx) {
+                const cudaError_t e = line_smem_limit<step_line_staged<Lat, N, Acc, true>, Lat>();
+                if (e != cudaSuccess) return e;
+                step_line_staged<Lat, N, Acc, true><<<v.ntiles, v.tile_width, smem, v.stream>>>(a, map);
+            } else {
+                const cudaError_t e = line_smem_limit<step_line_staged<Lat, N, Acc, false>, Lat>();
+                if (e != cudaSuccess) return e;
+                step_line_staged<Lat, N, Acc, false><<<v.ntiles, v.tile_width, smem, v.stream>>>(a, map);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (v.line) {
         if (v.fixedx)
             step_line_kernel<Lat, N, T, Acc, Split, true><<<v.ntiles, v.tile_width, 0, v.stream>>>(a);
@@ -167,6 +241,22 @@ cudaError_t launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, 
     cfg.numAttrs = 1;
     const int ntiles = v.ntiles;
     unsigned *bar = v.bar;
+    if constexpr (Split) {
+        CUtensorMap ma, mb;
+        if (line_encode_map<Lat>(v, fa, &ma) && line_encode_map<Lat>(v, fb, &mb)) {
+            cfg.dynamicSmemBytes = LineStage<Lat>::persistent_bytes(v.tile_width);
+            if (v.fixedx) {
+                const cudaError_t e = line_smem_limit<step_line_persistent_staged<Lat, N, Acc, true>, Lat>();
+                if (e != cudaSuccess) return e;
+                return cudaLaunchKernelEx(&cfg, step_line_persistent_staged<Lat, N, Acc, true>, a, nsteps, ntiles, bar,
+                                          ma, mb);
+            }
+            const cudaError_t e = line_smem_limit<step_line_persistent_staged<Lat, N, Acc, false>, Lat>();
+            if (e != cudaSuccess) return e;
+            return cudaLaunchKernelEx(&cfg, step_line_persistent_staged<Lat, N, Acc, false>, a, nsteps, ntiles, bar, ma,
+                                      mb);
+        }
+    }
     if (v.fixedx)
         return cudaLaunchKernelEx(&cfg, step_line_persistent<Lat, N, T, Acc, Split, true>, a, nsteps, ntiles, bar);
     return cudaLaunchKernelEx(&cfg, step_line_persistent<Lat, N, T, Acc, Split, false>, a, nsteps, ntiles, bar);
@@ -175,6 +265,24 @@ cudaError_t launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, 
 template <class Lat, int N, class T, class Acc, bool Split>
 int persistent_occupancy(const CtxView &v) {
     int n = 0;
+    if constexpr (Split) {
+        if (line_staging_applies<Lat>(v)) {
+            const size_t smem = LineStage<Lat>::persistent_bytes(v.tile_width);
+            cudaError_t e;
+            if (v.fixedx) {
+                e = line_smem_limit<step_line_persistent_staged<Lat, N, Acc, true>, Lat>();
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_line_persistent_staged<Lat, N, Acc, true>,
+                                                                      v.tile_width, smem);
+            } else {
+                e = line_smem_limit<step_line_persistent_staged<Lat, N, Acc, false>, Lat>();
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_line_persistent_staged<Lat, N, Acc, false>,
+                                                                      v.tile_width, smem);
+            }
+            return e == cudaSuccess ? n : 0;
+        }
+    }
     const cudaError_t e =
         v.fixedx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_line_persistent<Lat, N, T, Acc, Split, true>,
                                                                  v.tile_width, 0)
@@ -213,24 +321,6 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
     a.step = v.step;
     a.tma = 0;
     return a;
-}
-
-// cuTensorMapEncodeTiled, looked up through the runtime (no link-time dependence on the
-// driver library).
-using TensorMapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
-                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                       CUtensorMapFloatOOBfill);
-inline TensorMapEncodeFn tensor_map_encoder() {
-    static const TensorMapEncodeFn fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return TensorMapEncodeFn(nullptr);
-        return reinterpret_cast<TensorMapEncodeFn>(p);
-    }();
-    return fn;
 }
 
 // Tensor map of a state for the warp-staged kernels: [Q planes][stride elements], box of

@@ -21,6 +21,7 @@
 // constant times (A = 0, B = tau_c + 1/2).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded by the host)
 #include <cuda_runtime.h>
 
 #include "core.cuh"
@@ -179,30 +180,17 @@ SMRT_D ff ff_inv() {
     return ff{hi, lo};
 }
 
-// Fixed point: x 2^S rounded to the nearest integer (ties away from zero), formed from the
-// float's bit pattern with integer instructions. Sums of such integers are exact and
-// independent of their order. Valid for |x| < 2^(62 - S); magnitudes below 2^-(S + 1) give 0,
-// as do zeros and subnormals. The split-precision step keeps populations and raw moments at
-// S = kFix (2^-44 resolution, range 2^19) and the equilibrium's monomial coefficients at
-// S = kFixP (2^-48, range 2^14).
+// Fixed point: x 2^S rounded to the nearest integer (the hardware conversion of the exactly
+// scaled float). Sums of such integers are exact and independent of their order. Valid for
+// |x| < 2^(62 - S); magnitudes below 2^-(S + 1) give 0. The split-precision step keeps
+// populations and raw moments at S = kFix (2^-44 resolution, range 2^18) and the equilibrium's
+// monomial coefficients at S = kFixP (2^-48, range 2^14).
 constexpr int kFix = 44;
 constexpr int kFixP = 48;
+constexpr float pow2f(int e) { return e >= 0 ? float(1ull << e) : 1.0f / float(1ull << -e); }
 template <int S = kFix>
 SMRT_D long long to_fixed(float x) {
-    const unsigned b = __float_as_uint(x);
-    const int e = int((b >> 23) & 0xffu);
-    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // |x| = m 2^(e - 150)
-    const int s = e - 150 + S;
-    unsigned long long mag;
-    if (s >= 0) {
-        mag = m << (s < 39 ? s : 39);
-    } else {
-        const int r = -s < 31 ? -s : 31;
-        mag = (m + (1ull << (r - 1))) >> r;
-    }
-    if (e == 0) mag = 0;
-    const long long q = static_cast<long long>(mag);
-    return (b >> 31) ? -q : q;
+    return __float2ll_rn(x * pow2f(S));
 }
 template <int S = kFix>
 SMRT_D long long to_fixed(double x) {
@@ -227,7 +215,6 @@ struct SplitAcc {
 
 // q 2^-S as a two-float number: q = a 2^48 + b 2^24 + c with 0 <= b, c < 2^24, each piece
 // exact as a float
-constexpr float pow2f(int e) { return e >= 0 ? float(1ull << e) : 1.0f / float(1ull << -e); }
 template <int S = kFix>
 SMRT_D ff fixed_to_ff(long long q) {
     const float a = float(int(q >> 48)) * pow2f(48 - S);
@@ -848,6 +835,64 @@ struct Collide {
     }
 };
 
+// ------------------------------------------------------------------------------ async copies (sm_90+)
+SMRT_D unsigned smem_addr(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+SMRT_D void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+SMRT_D void mbar_arrive_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+// One contiguous global -> shared copy by the bulk-copy engine; its bytes count against the
+// transaction count of mbarrier b. Addresses and size must be multiples of 16 bytes.
+SMRT_D void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(b))
+                 : "memory");
+}
+// One box of a 2D tensor map (coordinates: element within the plane, plane) -> shared memory,
+// bytes counted against mbarrier b. The x coordinate must be a multiple of 16 bytes; the
+// destination is 128-byte aligned. Elements outside the tensor read as zero.
+SMRT_D void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_addr(b))
+        : "memory");
+}
+// Order this thread's earlier generic-proxy accesses of shared (global) memory before its
+// later async-proxy ones: a buffer read or written by the threads, then refilled by the copy
+// engine; data written by other blocks, then copied.
+SMRT_D void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+SMRT_D void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Make mbarrier initialisations visible to the async proxy (the copy engine).
+SMRT_D void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+SMRT_D unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait until the phase of parity `parity` of mbarrier b has completed. Gives up after about a
+// second (or 2^26 polls) and returns false.
+SMRT_D bool mbar_wait(unsigned long long *b, unsigned parity) {
+    const unsigned addr = smem_addr(b);
+    const unsigned long long t0 = global_ns();
+    for (unsigned spin = 0; spin < (1u << 26); ++spin) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 63u) == 63u && global_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------------------------ loaders
 // Blocks of 128 threads per SM that the step kernels leave room for (0: no minimum, the
 // compiler's own register choice). The split-precision collision would take all 255 registers
@@ -1026,6 +1071,147 @@ __global__ void __launch_bounds__(128, kStepMinBlocks<Split>) step_line_persiste
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) bar[2] = step0 + unsigned(nsteps);
+}
+
+// ------------------------------------------------------------------------------ staged lines
+// Split-precision batched lines with the pulls staged in shared memory. Each warp owns 32
+// consecutive cells of a tile; every pull of those cells from the previous state lies in the
+// x-segment [base + x0 - k - E, base + x0 + 31 - k + E] of each population plane (E the largest
+// |e_x|), so one box of a 2D tensor map of the state ([Q planes][stride cells], library plane
+// order), rounded out to 16 bytes, brings all Q rows in by one copy, completion counted in
+// bytes on the warp's mbarrier. The lanes then read their pulls from shared memory instead of
+// issuing Q dependent loads each. Pulls from beyond a fixed end read the end states (in
+// double, exactly) and wrapped pulls of a periodic line read the state directly.
+template <class Lat>
+struct LineStage {
+    static constexpr int kEmax = [] {
+        int m = 0;
+        for (int p = 0; p < Lat::NP; ++p) m = Lat::e(p, 0) > m ? Lat::e(p, 0) : (-Lat::e(p, 0) > m ? -Lat::e(p, 0) : m);
+        return m;
+    }();
+    static constexpr int kSeg = (32 + 2 * kEmax + 3 + 3) / 4 * 4;  // elements per staged row
+    static constexpr size_t kRows = size_t(kSeg) * Lat::Q * sizeof(float);
+    static constexpr size_t kWarpBytes = 128 + (kRows + 127) / 128 * 128;  // mbarrier, then rows
+    SMRT_HD static size_t bytes(int threads) { return size_t(threads / 32) * kWarpBytes; }
+    // the persistent kernel keeps a block-wide failure flag after the warps' areas
+    SMRT_HD static size_t persistent_bytes(int threads) { return bytes(threads) + 16; }
+};
+
+// One warp's 32 cells of tile tile_index. All lanes call it. Returns false (LB_HEALTH_TIMEOUT
+// recorded) when the copy did not land within the bounded wait.
+template <class Lat, int N, class Acc, bool FixedX, bool Coherent>
+SMRT_D bool line_warp_staged(const StepArgs<Lat, float> &a, const float *__restrict__ fin, float *__restrict__ fout,
+                             int tile_index, unsigned step, unsigned long long *bar, float *buf, unsigned &parity,
+                             const CUtensorMap *tm) {
+    using C = Collide<Lat, N, float, Acc, true>;
+    using S = LineStage<Lat>;
+    const int lane = threadIdx.x & 31;
+    const int2 tile = a.tiles[tile_index];
+    const InstanceInfo &in = a.inst[tile.x];
+    const int xw = tile.y + int(threadIdx.x & ~31u);  // the warp's first cell
+    const int L = in.nx;
+    if (xw >= L) return true;  // the whole warp lies beyond the line's end
+    const long long base = in.cell_off;
+    const long long g_al = (base + xw - in.kx - S::kEmax) & ~3ll;  // first staged element, 16-byte aligned
+    // the previous tile's reads of buf (generic proxy) and, in a persistent launch, other
+    // blocks' writes of the state come before the copy engine's accesses
+    __syncwarp();
+    if (lane == 0) {
+        if constexpr (Coherent) fence_async_global();
+        fence_async_shared();
+        mbar_arrive_expect_tx(bar, unsigned(S::kRows));
+        tma_load_2d(buf, tm, int(g_al), 0, bar);
+    }
+    const bool landed = __all_sync(0xffffffffu, mbar_wait(bar, parity));
+    if (!landed) {
+        if (lane == 0) atomicOr(a.health, 2u);
+        mbar_wait(bar, parity);  // let the copy in flight land before leaving (bounded)
+        return false;
+    }
+    parity ^= 1u;
+    const int x = xw + lane;
+    if (x >= L) return true;
+    const double *gld = a.ghostsd + (long long)tile.x * 2 * Lat::Q;
+    const double *grd = gld + Lat::Q;
+    const int tb = int(base + x - in.kx - g_al);  // staged offset of this lane's pull with e_x = 0
+    bool finite = true;
+    auto pullq = [&](auto I) -> long long {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = i == 0 ? 0 : ((i & 1) ? Lat::e((i - 1) / 2, 0) : -Lat::e((i - 1) / 2, 0));
+        const int xs = x - ex - in.kx;
+        float v;
+        if (xs < 0 || xs >= L) {
+            if constexpr (FixedX) return to_fixed(xs < 0 ? gld[i] : grd[i]);
+            v = load_pop<Coherent>(fin + a.plane[i] + base + wrap(xs, L));
+        } else {
+            v = buf[i * S::kSeg + tb - ex];
+        }
+        finite &= (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+        return to_fixed(v);
+    };
+    const bool ok = C::collide_split(pullq, [&](int i, float v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wlo,
+                                     a.c, a.clo, tau_a<float>(in), tau_b<float>(in),
+                                     mix32(unsigned(base + x) ^ mix32(step)));
+    if (!(ok && finite)) atomicOr(a.health, 1u);
+    return true;
+}
+
+// Warp w of a block takes the warp part w of tile blockIdx.x (tile width = block size).
+template <class Lat, int N, class Acc, bool FixedX>
+__global__ void __launch_bounds__(128, kStepMinBlocks<true>) step_line_staged(StepArgs<Lat, float> a,
+                                                                               const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    unsigned char *w = dyn + size_t(threadIdx.x >> 5) * LineStage<Lat>::kWarpBytes;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(w);
+    float *buf = reinterpret_cast<float *>(w + 128);
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    unsigned parity = 0u;
+    line_warp_staged<Lat, N, Acc, FixedX, false>(a, a.fin, a.fout, blockIdx.x, a.step, bar, buf, parity, &map);
+}
+
+// All nsteps steps in one cooperative launch (as step_line_persistent), the pulls staged.
+template <class Lat, int N, class Acc, bool FixedX>
+__global__ void __launch_bounds__(128, kStepMinBlocks<true>) step_line_persistent_staged(
+    StepArgs<Lat, float> a, int nsteps, int ntiles, unsigned *barg, const __grid_constant__ CUtensorMap map_a,
+    const __grid_constant__ CUtensorMap map_b) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    int &failed = *reinterpret_cast<int *>(dyn + LineStage<Lat>::bytes(blockDim.x));
+    unsigned char *w = dyn + size_t(threadIdx.x >> 5) * LineStage<Lat>::kWarpBytes;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(w);
+    float *buf = reinterpret_cast<float *>(w + 128);
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (threadIdx.x == 0) failed = 0;
+    __syncthreads();
+    unsigned parity = 0u;
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = atomicAdd(&barg[1], 0u);
+    const unsigned step0 = __ldcg(&barg[2]);
+    const float *src = a.fin;
+    float *dst = a.fout;
+    for (int s = 0; s < nsteps; ++s) {
+        const CUtensorMap *tm = src == a.fin ? &map_a : &map_b;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+            if (!line_warp_staged<Lat, N, Acc, FixedX, true>(a, src, dst, t, step0 + unsigned(s), bar, buf, parity, tm)) {
+                failed = 1;  // the warp stops (its lanes agree); the block leaves after this step
+                break;
+            }
+        __syncthreads();
+        if (failed) return;
+        if (s + 1 < nsteps) {
+            if (!grid_barrier(barg, gen, a.health)) return;
+            const float *nsrc = dst;
+            dst = (dst == a.fout) ? const_cast<float *>(a.fin) : a.fout;
+            src = nsrc;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) barg[2] = step0 + unsigned(nsteps);
 }
 
 // ------------------------------------------------------------------------------ moments

@@ -20,7 +20,6 @@
 // Ghost populations (end states beyond a fixed x end) are kept in library order.
 #pragma once
 
-#include <cuda.h>  // CUtensorMap (the type only; maps are encoded by the host)
 
 #include "kernels.cuh"
 #include "moment_tables.cuh"
@@ -686,64 +685,6 @@ struct TPCell {
         to_rebuild<U>(ta, c, P);
     }
 };
-
-// ------------------------------------------------------------------ async copies (sm_90+)
-SMRT_D unsigned smem_addr(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
-
-SMRT_D void mbar_init(unsigned long long *b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-SMRT_D void mbar_arrive_expect_tx(unsigned long long *b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
-                 : "memory");
-}
-// One contiguous global -> shared copy by the bulk-copy engine; its bytes count against the
-// transaction count of mbarrier b. Addresses and size must be multiples of 16 bytes.
-SMRT_D void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(b))
-                 : "memory");
-}
-// One box of a 2D tensor map (coordinates: element within the plane, plane) -> shared memory,
-// bytes counted against mbarrier b. The x coordinate must be a multiple of 16 bytes; the
-// destination is 128-byte aligned. Elements outside the tensor read as zero.
-SMRT_D void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, unsigned long long *b) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_addr(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(smem_addr(b))
-        : "memory");
-}
-// Order this thread's earlier generic-proxy accesses of shared (global) memory before its
-// later async-proxy ones: a buffer read or written by the threads, then refilled by the copy
-// engine; data written by other blocks, then copied.
-SMRT_D void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-SMRT_D void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-// Make mbarrier initialisations visible to the async proxy (the copy engine).
-SMRT_D void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-SMRT_D unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait until the phase of parity `parity` of mbarrier b has completed. Gives up after about a
-// second (or 2^26 polls) and returns false.
-SMRT_D bool mbar_wait(unsigned long long *b, unsigned parity) {
-    const unsigned addr = smem_addr(b);
-    const unsigned long long t0 = global_ns();
-    for (unsigned spin = 0; spin < (1u << 26); ++spin) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((spin & 63u) == 63u && global_ns() - t0 > 1000000000ull) return false;
-    }
-    return false;
-}
 
 // ------------------------------------------------------------------ warp-staged line tile
 // Each warp owns a tile of 32 cells and its own copy pipeline, so no block-wide barrier is

@@ -80,6 +80,31 @@ def test_box_steps_match_oracle(lats, name, N, prec, tol):
     assert P.lb_poll_status(ctx)[0] == 0
 
 
+@pytest.mark.parametrize("name,N,nx,shift", [("D3Q103", 4, 150, 1), ("D3Q39", 3, 70, 2), ("D3Q103", 4, 20, 0)])
+def test_periodic_line_split_precision_matches_oracle(lats, name, N, nx, shift):
+    """Split precision on a periodic line (staged pulls; wrapped pulls read the state directly):
+    several 32-cell warp parts and a ragged tail, and a line shorter than one warp, 1 and 3
+    steps from a perturbed state."""
+    olat, d, idx = lats[name]
+    shape = (1, 1, nx)
+    model = OS.Model(olat, N, tau_ref=0.9)
+    geom = OS.Geometry(shape=shape, shift=(shift, 0, 0))
+    f0 = _perturbed_box(olat, N, shape).reshape(olat.q, *shape)
+    ctx = P.lb_init_lattice(_desc(d, (shift, 0, 0)), nx, N=N, precision="f32c64", bc_x=0)
+    P.lb_set_relaxation(ctx, _tau(model), True, 1.0)
+    fa = upload(ctx, f0, idx)
+    f0 = download(ctx, fa, idx).reshape(f0.shape)
+    fb = ctx.new_state()
+    for nsteps in (1, 3):
+        want = f0
+        for _ in range(nsteps):
+            want = OS.step(want, model, geom)
+        got = download(ctx, P.lb_step(ctx, upload(ctx, f0, idx), fb, nsteps), idx)
+        err = np.abs(got - want.reshape(olat.q, -1)).max() / np.abs(want).max()
+        assert err < 2e-6 * nsteps, (nsteps, err)
+    assert P.lb_poll_status(ctx)[0] == 0
+
+
 @pytest.mark.parametrize("name,N,prec,tol", [("D3Q39", 3, "f64", 1e-13), ("D3Q39", 3, "f32", 1e-7),
                                               ("D3Q103", 4, "f64", 1e-13)])
 def test_fill_equilibrium_matches_oracle(lats, name, N, prec, tol):

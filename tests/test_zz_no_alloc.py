@@ -60,3 +60,29 @@ def test_noalloc_adjoint_matches_allocating_entry_point():
         np.testing.assert_allclose(got_dtau.cpu().numpy(), ref_dtau.cpu().numpy(), rtol=1e-12, atol=0)
     assert P.lb_poll_status(ctx)[0] == 0
     ctx.close()
+
+
+def test_noalloc_adjoint_rejects_grids_beyond_its_array():
+    """A line context scheduled at 32-cell tiles with more tiles (8438) than the fixed array has
+    slots (8192) is refused with LB_ERR_INVALID before any launch: lam_t and dtau keep their
+    contents. At 128-cell tiles (2110 tiles) the same context is accepted."""
+    d = P.lb_lattice_named("D3Q39")
+    nx = 270000
+    ctx = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree, (1, 0, 0)), nx, N=3, precision="f64",
+                            bc_x=1)
+    left, right = P.lb_rankine_hugoniot(1.2, theta1=1.0)
+    P.lb_set_relaxation(ctx, [2.4, 2.4, 1.6, 3.6], True, 1.0, left, right)
+    lib = _ffi.lib()
+    f = ctx.new_state()
+    lam_next = torch.ones(ctx.state_elems, dtype=torch.float64, device="cuda")
+    lam_t = torch.full_like(lam_next, 7.0)
+    dtau = torch.full((4,), 3.0, dtype=torch.float64, device="cuda")
+    P.lb_set_schedule(ctx, 32, 0, 0)
+    assert lib.lb_step_adjoint_noalloc(ctx.handle, _vp(f), _vp(lam_next), _vp(lam_t), _vp(dtau)) == 1
+    torch.cuda.synchronize()
+    assert bool((lam_t == 7.0).all()) and bool((dtau == 3.0).all())
+    P.lb_set_schedule(ctx, 128, 0, 0)
+    assert lib.lb_step_adjoint_noalloc(ctx.handle, _vp(f), _vp(lam_next), _vp(lam_t), _vp(dtau)) == 0
+    torch.cuda.synchronize()
+    assert P.lb_poll_status(ctx)[0] == 0
+    ctx.close()
