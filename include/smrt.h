@@ -335,6 +335,12 @@ lb_status lb_rankine_hugoniot(double Ma, double gamma, double rho1, double theta
  * Host memory out. Errors: LB_ERR_INVALID. */
 lb_status lb_shock_frame(double Ma, double gamma, double c, double theta2_max, double *theta1, int *kx);
 
+/* lb_shock_shift -- the frame shift of lb_shock_frame for a given upstream temperature theta1
+ * (e.g. Table 3's): *kx = round(((u1 + u2)/2) / c) with (u1 + u2)/2 =
+ * (gamma Ma^2 + 1) / ((gamma + 1) Ma) sqrt(gamma theta1) (Sec. 4.1-4.2). Host memory out.
+ * Errors: LB_ERR_INVALID (null, Ma < 1, gamma <= 1, c <= 0, theta1 <= 0). */
+lb_status lb_shock_shift(double Ma, double gamma, double c, double theta1, int *kx);
+
 const char *lb_error_string(lb_status status);
 void lb_destroy(lb_ctx *ctx);
 

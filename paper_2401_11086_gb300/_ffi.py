@@ -60,6 +60,7 @@ SIGNATURES = {
     "lb_lattice_named": (c_int, [c_char_p, POINTER(c_int8), POINTER(c_double), POINTER(c_double), POINTER(c_int), POINTER(c_int), c_int]),
     "lb_rankine_hugoniot": (c_int, [c_double, c_double, c_double, c_double, POINTER(LbState), POINTER(LbState)]),
     "lb_shock_frame": (c_int, [c_double, c_double, c_double, c_double, POINTER(c_double), POINTER(c_int)]),
+    "lb_shock_shift": (c_int, [c_double, c_double, c_double, c_double, POINTER(c_int)]),
     "lb_error_string": (c_char_p, [c_int]),
     "lb_destroy": (None, [c_void_p]),
 }

@@ -74,6 +74,13 @@ def lb_shock_frame(Ma: float, c: float, gamma: float = 5.0 / 3.0, theta2_max: fl
     return t1.value, k.value
 
 
+def lb_shock_shift(Ma: float, c: float, theta1: float, gamma: float = 5.0 / 3.0) -> int:
+    """kx: frame shift of a normal shock for a given upstream temperature."""
+    k = c_int()
+    _check(_ffi.lib().lb_shock_shift(Ma, gamma, c, theta1, byref(k)), "lb_shock_shift")
+    return k.value
+
+
 def lb_error_string(status: int) -> str:
     return _ffi.lib().lb_error_string(status).decode()
 

@@ -326,9 +326,14 @@ extern "C" lb_status lb_shock_frame(double Ma, double gamma, double c, double th
     const double ratio = r.theta;  // theta2 / theta1
     // the hottest state must stay below the convergence bound theta < 2 (Sec. 4.1)
     const double t1 = (ratio < 2.0 && Ma <= 1.9) ? 1.0 : theta2_max / ratio;
-    const double c1 = std::sqrt(gamma * t1);
-    const double mean = (gamma * Ma * Ma + 1.0) / ((gamma + 1.0) * Ma) * c1;  // (u1 + u2) / 2
     *theta1 = t1;
+    return lb_shock_shift(Ma, gamma, c, t1, kx);
+}
+
+extern "C" lb_status lb_shock_shift(double Ma, double gamma, double c, double theta1, int *kx) {
+    if (!kx || !(Ma >= 1.0) || !(gamma > 1.0) || !(c > 0.0) || !(theta1 > 0.0)) return LB_ERR_INVALID;
+    const double c1 = std::sqrt(gamma * theta1);
+    const double mean = (gamma * Ma * Ma + 1.0) / ((gamma + 1.0) * Ma) * c1;  // (u1 + u2) / 2
     *kx = (int)std::lround(mean / c);
     return LB_OK;
 }

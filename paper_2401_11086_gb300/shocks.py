@@ -48,12 +48,10 @@ def shock_params(Ma: float, c: float, N: int, ell_cells: float = 2.0, ratios=TAU
                  theta2_max: float = 1.2, theta1: float | None = None):
     """End states, frame shift and continuous relaxation times of one shock. theta1 overrides
     the reference temperature (e.g. a Table 3 value); the frame shift follows it."""
-    t1, kx = api.lb_shock_frame(Ma, c, GAMMA, theta2_max)
-    if theta1 is not None and theta1 != t1:
-        # k = round(((u1 + u2) / 2) / c) with the given upstream temperature
-        mean = (GAMMA * Ma * Ma + 1.0) / ((GAMMA + 1.0) * Ma) * np.sqrt(GAMMA * theta1)
-        t1, kx = theta1, int(np.floor(mean / c + 0.5))
-    theta1 = t1
+    if theta1 is None:
+        theta1, kx = api.lb_shock_frame(Ma, c, GAMMA, theta2_max)
+    else:
+        kx = api.lb_shock_shift(Ma, c, theta1, GAMMA)
     left, right = api.lb_rankine_hugoniot(Ma, GAMMA, 1.0, theta1)
     tau20 = ell_cells * c / np.sqrt(theta1)
     taus = [r * tau20 for r in ratios[: ntau(N)]]

@@ -126,3 +126,15 @@ def test_library_shock_frame_agrees_with_oracle(lib, Ma):
         t1, k = P.lb_shock_frame(Ma, c)
         assert abs(t1 - OK.theta_scale(Ma)) < 1e-14
         assert k == OK.shift(Ma, t1, c)
+
+
+def test_library_shock_shift_reproduces_table3(lib):
+    """Table 3: with its printed theta1 and c_l, the frame shift is k_x = 2 on D1Q9-P1 (Ma 1.5,
+    3, 5) and 3 on D1Q17-P1 (Ma 7); the library agrees with the oracle's rule."""
+    import paper_2401_11086_gb300 as P
+    from _golden import rows
+    for r in rows("table3_implementation.txt"):
+        Ma, c_l, th1, kx = float(r[0]), float(r[3]), float(r[5]), int(float(r[7]))
+        assert P.lb_shock_shift(Ma, c_l, th1) == kx == OK.shift(Ma, th1, c_l)
+    with pytest.raises(P.SmrtError):
+        P.lb_shock_shift(3.0, 1.0, 0.0)
