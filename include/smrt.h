@@ -329,8 +329,9 @@ lb_status lb_rankine_hugoniot(double Ma, double gamma, double rho1, double theta
                               lb_state *left, lb_state *right);
 
 /* lb_shock_frame -- reference temperature and frame shift of a normal shock (Sec. 4.1-4.2):
- * *theta1 = 1 when the downstream temperature stays below 2 (Ma <= 1.9), else the upstream
- * temperature that puts the downstream one at theta2_max (< 2, the Hermite convergence bound);
+ * *theta1 = min(1, theta2_max / (theta2/theta1)): 1 when the downstream temperature stays at
+ * or below theta2_max, else the upstream temperature that puts the downstream one at
+ * theta2_max (well below 2, the Hermite convergence bound);
  * *kx = round(((u1 + u2)/2) / c), the integer shift minimising the largest relative speed.
  * Host memory out. Errors: LB_ERR_INVALID. */
 lb_status lb_shock_frame(double Ma, double gamma, double c, double theta2_max, double *theta1, int *kx);

@@ -6,9 +6,12 @@
 * ``mean_speed``: (u1 + u2)/2 = (gamma Ma^2 + 1)/((gamma+1) Ma) c1 (Sec. 4.2).
 * ``shift``: k_x = round(((u1 + u2)/2) / c), the integer frame shift of Sec. 4.1; reproduces
   every k_x and u_bar_x of Table 3.
-* ``theta_scale``: the reference temperature is chosen so that the hottest state stays below
-  the Hermite convergence bound theta < 2 (Sec. 4.1): theta1 = 1 when the downstream state is
-  already below 2 at theta1 = 1 (Ma < ~1.94), otherwise theta2 = ``theta2_target``.
+* ``theta_scale``: the reference temperature is chosen so that the hottest state stays well
+  below the Hermite convergence bound theta < 2 (Sec. 4.1): theta1 = 1 when the downstream
+  state is at most ``theta2_target`` (1.2) at theta1 = 1, otherwise theta2 = ``theta2_target``,
+  i.e. theta1 = min(1, theta2_target / (theta2/theta1)). The paper lowers theta1 below 1 even
+  where theta2 would stay below 2 (Table 3, Ma = 1.5: theta1 = 0.714, theta2 = 1.07), and a
+  downstream state at theta2 = 1.94 (Ma = 1.89 with theta1 = 1) is unstable on D3Q729.
 * ``tau_from_mean_free_path``: the upstream mean free path in cells is
   ell = tau_c sqrt(theta1) / c (time in steps, cell size c), so tau_c = ell c / sqrt(theta1).
   The paper's Kn definition (Sec. 4.2) is dimensionally garbled; this is the reading used.
@@ -49,9 +52,7 @@ def half_jump(Ma: float, theta1: float, gamma: float = GAMMA) -> float:
 def theta_scale(Ma: float, theta2_target: float = 1.2, gamma: float = GAMMA) -> float:
     """Upstream theta1 in units of the reference temperature."""
     ratio = rankine_hugoniot(Ma, gamma)["theta2"]
-    if ratio < 2.0 and Ma <= 1.9:
-        return 1.0
-    return theta2_target / ratio
+    return min(1.0, theta2_target / ratio)
 
 
 def shift(Ma: float, theta1: float, c: float, gamma: float = GAMMA) -> int:

@@ -11,6 +11,7 @@
 // up to degree Q - 1 (Q odd). For fixed c the first S patterns (by ascending degree) fix the
 // weights through an S x S linear solve; the last pattern's residual r(c) is then a scalar
 // function of c whose root is found by bracketing and bisection.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -324,8 +325,8 @@ extern "C" lb_status lb_shock_frame(double Ma, double gamma, double c, double th
     lb_state l, r;
     lb_rankine_hugoniot(Ma, gamma, 1.0, 1.0, &l, &r);
     const double ratio = r.theta;  // theta2 / theta1
-    // the hottest state must stay below the convergence bound theta < 2 (Sec. 4.1)
-    const double t1 = (ratio < 2.0 && Ma <= 1.9) ? 1.0 : theta2_max / ratio;
+    // the hottest state must stay well below the convergence bound theta < 2 (Sec. 4.1)
+    const double t1 = std::min(1.0, theta2_max / ratio);
     *theta1 = t1;
     return lb_shock_shift(Ma, gamma, c, t1, kx);
 }

@@ -418,3 +418,35 @@ def test_graph_needs_a_persistent_schedule(lat):
     P.lb_set_schedule(ctx, 32, 1, 1)
     out = P.lb_step_graph(ctx, f0.clone(), ctx.new_state(), 4)
     assert P.lb_poll_status(ctx)[0] == 0 and torch.isfinite(out).all()
+
+
+# ------------------------------------------------------------------ mixed-Mach batch, graph path
+@pytest.mark.parametrize("prec,tol_rho,tol_q", [("f64", 1e-10, 1e-9), ("f32", 5e-5, 1e-4)])
+def test_mixed_mach_batch_graph_replay_against_golden(lat, prec, tol_rho, tol_q):
+    """Shocks at Ma 1.5 / 2.5 / 4 / 5 on D3Q729 (N = 5, reference temperature of reading 11,
+    tanh width 10, 80-140 cells), batched in one context and run as one persistent launch of
+    1000 steps captured in a CUDA graph (lb_step_graph): rho, theta and q_x of every instance
+    against the oracle's stored profiles (tests/golden/make_shock_golden.py mixed_d3q729_n5).
+    FP64 to round-off; FP32 populations (no split precision on this set) to the stated
+    tolerances, relative to rho, theta and to the instance's largest |q_x|."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "mixed_d3q729_n5.npz")
+    gold = np.load(path)
+    olat, d, idx = lat
+    machs = [float(m) for m in gold["machs"]]
+    lengths = [int(n) for n in gold["nx"]]
+    ctx, f0, params = shocks.setup_batch(d, 5, machs, lengths, precision=prec, width=10.0)
+    for j, p in enumerate(params):
+        assert p["kx"] == int(gold[f"k_{j}"]) and abs(p["theta1"] - float(gold[f"theta1_{j}"])) < 1e-14
+    P.lb_set_schedule(ctx, 64, 0, 1)
+    fb = ctx.new_state()
+    out = P.lb_step_graph(ctx, f0, fb, 1000)
+    assert P.lb_poll_status(ctx)[0] == 0
+    m = P.lb_moments(ctx, out, P.LB_MOM_RHO | P.LB_MOM_U | P.LB_MOM_THETA | P.LB_MOM_Q).cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    for j in range(len(machs)):
+        s = slice(off[j], off[j + 1])
+        rho, th, q = gold[f"rho_1000_{j}"], gold[f"theta_1000_{j}"], gold[f"q_1000_{j}"]
+        assert np.abs(m[0][s] / rho - 1).max() < tol_rho, (j, machs[j])
+        assert np.abs(m[4][s] / th - 1).max() < tol_rho, (j, machs[j])
+        assert np.abs(m[5][s] - q).max() / np.abs(q).max() < tol_q, (j, machs[j])
+    ctx.close()

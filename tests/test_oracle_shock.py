@@ -193,3 +193,30 @@ def test_degree9_upstream_stability_boundary():
     initial level, at Ma 3.25 it has grown more than tenfold after 600 steps."""
     assert _upstream_noise_growth(2.5) < 2e-6
     assert _upstream_noise_growth(3.25) > 1e-5
+
+
+def _upstream_noise_growth_d3q729(Ma, theta1, steps=400, nx=32):
+    """As _upstream_noise_growth, on the paper's D3Q729 set with N = 5; theta1 None: the
+    reference temperature of reading 11 (theta2 = 1.2). The growing mode needs a periodic line
+    of about 32 cells (16 and 24 cells hold none)."""
+    lat = L.d3q729()
+    case = K.shock_case(lat, 5, Ma, nx, theta1=theta1)
+    st = case.states
+    rng = np.random.default_rng(0)
+    rho = st["rho1"] * (1 + 1e-6 * rng.standard_normal(nx))
+    u = np.stack([np.full(nx, st["u1"] - lat.c * case.k), np.zeros(nx), np.zeros(nx)])
+    h = S.equilibrium(rho, u, np.full(nx, st["theta1"]), lat, 5).reshape(lat.q, 1, 1, nx)
+    geom = S.Geometry(shape=(1, 1, nx), shift=(case.k, 0, 0))
+    for _ in range(steps):
+        h = S.step(h, case.model, geom)
+    m = S.macroscopic(h, case.model, geom)
+    return float(np.max(np.abs(m["rho"] / st["rho1"] - 1)))
+
+
+def test_degree11_upstream_stability_needs_the_theta2_reference():
+    """On D3Q729 the Ma = 5 upstream state is stable with the reference temperature of reading
+    11 (theta2 = 1.2: seeded 1e-6 noise decays) and linearly unstable with Table 3's own
+    theta1 = 0.167 (theta2 = 1.45: more than tenfold growth in 400 steps). The paper's 100-cell
+    runs end before the growth shows; the long batched shocks on this set use reading 11."""
+    assert _upstream_noise_growth_d3q729(5.0, None) < 1e-6
+    assert _upstream_noise_growth_d3q729(5.0, 0.167) > 1e-5
