@@ -155,9 +155,12 @@ lb_status lb_set_frame_shift(lb_ctx *ctx, int instance, int kx);
  * toward the coefficients of that Gaussian, truncated at N. The discrete scheme uses
  * b' = 1 - (1 - b) tau_20 / (tau_20 - b/2), which keeps the continuous model's stress rate
  * (1 - b)/tau_c under the second-order discretisation, so Pr = 1/(1 - b) (2/3 at b = -1/2).
- * Requires -1/2 <= b < 1. Tensor-product sets (D3Q729, D3Q4913) only. Stored on the host and
- * uploaded as lb_set_relaxation's settings are.
- * Errors: LB_ERR_INVALID (instance, model or b), LB_ERR_UNSUPPORTED (other sets), LB_ERR_CUDA. */
+ * Requires -1/2 <= b < 1. Every velocity set and precision (with LB_F32_CONS64 the relaxation
+ * acts on the non-equilibrium part, which in the local frame is the whole of orders >= 2). The
+ * adjoint calls (lb_step_adjoint, lb_step_adjoint_noalloc) differentiate SMRT only and return
+ * LB_ERR_UNSUPPORTED while any instance uses ES-BGK. Stored on the host and uploaded as
+ * lb_set_relaxation's settings are.
+ * Errors: LB_ERR_INVALID (instance, model or b), LB_ERR_CUDA. */
 lb_status lb_set_collision_model(lb_ctx *ctx, int instance, int model, double b);
 
 /* lb_fill_equilibrium -- f = order-N truncated Maxwellian of the given fields at every cell
@@ -250,7 +253,8 @@ lb_status lb_moments(lb_ctx *ctx, const void *f, double *out, unsigned which_mas
  * times tau_c,nm. Arithmetic is double whatever the precision of f_t. Populations pulled from
  * beyond a fixed x end are constants (no gradient). The per-block gradient partials live in a
  * scratch array owned by the context; calls on one context must not overlap.
- * Errors: LB_ERR_INVALID (null, lam_next overlapping lam_t, relaxation unset), LB_ERR_CUDA. */
+ * Errors: LB_ERR_INVALID (null, lam_next overlapping lam_t, relaxation unset), LB_ERR_UNSUPPORTED
+ * (a set without adjoint kernels, or an instance using the ES-BGK model), LB_ERR_CUDA. */
 lb_status lb_step_adjoint(lb_ctx *ctx, const void *f_t, const double *lam_next, double *lam_t,
                           double *dtau);
 

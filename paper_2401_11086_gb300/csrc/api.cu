@@ -403,6 +403,13 @@ lb_status flush_tables(lb_ctx *c) {
     return LB_OK;
 }
 
+// The adjoint kernels differentiate the SMRT collision only.
+bool any_es_bgk(const lb_ctx *c) {
+    for (const InstanceInfo &in : c->h_inst)
+        if (in.model != LB_MODEL_SMRT) return true;
+    return false;
+}
+
 void mark_ghosts(lb_ctx *c, int j0, int j1) {
     c->tables_dirty = true;
     if (!c->view.fixedx) return;
@@ -473,7 +480,6 @@ extern "C" lb_status lb_set_collision_model(lb_ctx *c, int instance, int model, 
     if (!c || instance < -1 || instance >= c->batch) return LB_ERR_INVALID;
     if (model != LB_MODEL_SMRT && model != LB_MODEL_ES_BGK) return LB_ERR_INVALID;
     if (model == LB_MODEL_ES_BGK && !(b >= -0.5 && b < 1.0)) return LB_ERR_INVALID;
-    if (model == LB_MODEL_ES_BGK && c->kind < 2) return LB_ERR_UNSUPPORTED;
     const int j0 = instance < 0 ? 0 : instance, j1 = instance < 0 ? c->batch : instance + 1;
     for (int j = j0; j < j1; ++j) {
         c->h_inst[j].model = model;
@@ -703,6 +709,7 @@ extern "C" lb_status lb_step_adjoint(lb_ctx *c, const void *f_t, const double *l
                                      double *dtau) {
     if (!c || !f_t || !lam_next || !lam_t || !dtau || lam_next == lam_t) return LB_ERR_INVALID;
     if (!c->relax_set || !c->as) return c->as ? LB_ERR_INVALID : LB_ERR_UNSUPPORTED;
+    if (any_es_bgk(c)) return LB_ERR_UNSUPPORTED;
     const size_t bytes = sizeof(double) * lb_state_elems(c);
     const char *a0 = reinterpret_cast<const char *>(lam_next), *b0 = reinterpret_cast<const char *>(lam_t);
     if (a0 < b0 + bytes && b0 < a0 + bytes) return LB_ERR_INVALID;
@@ -806,7 +813,7 @@ lb_status noalloc_scratch(double **out) {
 extern "C" lb_status lb_step_adjoint_noalloc(lb_ctx *c, const void *f_t, const double *lam_next, double *lam_t,
                                              double *dtau) {
     if (!c || !f_t || !lam_next || !lam_t || !dtau || lam_next == lam_t) return LB_ERR_INVALID;
-    if (!c->as) return LB_ERR_UNSUPPORTED;
+    if (!c->as || any_es_bgk(c)) return LB_ERR_UNSUPPORTED;
     if (!c->relax_set) return LB_ERR_INVALID;
     const size_t bytes = sizeof(double) * lb_state_elems(c);
     const char *a0 = reinterpret_cast<const char *>(lam_next), *b0 = reinterpret_cast<const char *>(lam_t);

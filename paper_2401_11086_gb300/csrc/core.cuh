@@ -262,4 +262,53 @@ SMRT_HD void relax_order(T (&d)[nmom(N)], const T (&s)[ntau(N)]) {
     });
 }
 
+// ------------------------------------------------------------------ ES-BGK relaxation
+// a5 for the ES-BGK model (Sec. 3, Eq. ES-BGK): every order n >= 2 relaxes at the one
+// discrete rate 1/tau_20 toward the local-frame coefficients of Holway's Gaussian of
+// covariance theta delta + b' sigma / rho. In divided form they are the monomial
+// coefficients of rho exp(t.B.t / 2), B = (b'/rho) D2: order 2 is b' v2, order 4 is
+// (b'^2 / (2 rho)) times the sum over ordered pairs of order-2 slots adding up to the slot,
+// odd orders are zero. b' = 1 - (1 - b) tau_20 / (tau_20 - b/2) keeps the continuous stress
+// rate (1 - b)/tau_c under the second-order scheme (tau -> tau + 1/2 per mode), so
+// Pr = 1/(1 - b).
+template <int N, class T>
+SMRT_D void relax_es_divided(T (&v)[nmom(N)], T rho, T A, T B, T b) {
+    constexpr int M = nmom(N);
+    const T tau = fma(B, rho, A) * rcp(rho);
+    const T om = rcp(tau);
+    const T bp = T(1) - (T(1) - b) * tau * rcp(fma(T(-0.5), b, tau));
+    const T s = T(1) - om;
+    T t4[M];
+    static_for<M>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        if constexpr (mi_order(p) == 4) {
+            T acc = T(0);
+            static_for<M>([&](auto Q1s) {
+                constexpr int q1 = decltype(Q1s)::value;
+                if constexpr (mi_order(q1) == 2) {
+                    static_for<M>([&](auto Q2s) {
+                        constexpr int q2 = decltype(Q2s)::value;
+                        if constexpr (mi_order(q2) == 2 && mi_comp(q1, 0) + mi_comp(q2, 0) == mi_comp(p, 0) &&
+                                      mi_comp(q1, 1) + mi_comp(q2, 1) == mi_comp(p, 1))
+                            acc = fma(v[q1], v[q2], acc);
+                    });
+                }
+            });
+            t4[p] = acc;
+        }
+    });
+    const T k4 = om * bp * bp * T(0.5) * rcp(rho);
+    const T s2 = fma(om, bp, s);
+    static_for<M>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        constexpr int n = mi_order(p);
+        if constexpr (n == 2)
+            v[p] *= s2;
+        else if constexpr (n == 4)
+            v[p] = fma(k4, t4[p], s * v[p]);
+        else if constexpr (n >= 3)
+            v[p] *= s;
+    });
+}
+
 }  // namespace smrt

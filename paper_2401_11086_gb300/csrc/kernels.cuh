@@ -549,16 +549,22 @@ struct Collide {
     // a4-a6 on divided absolute coefficients v: to the local frame, relaxation of orders 2..N
     // with their own times, back to the absolute frame (truncated at N); the slot of order 0
     // leaves as o0 and those of order 1 as zero (u is the frame velocity).
+    // model 1: the ES-BGK relaxation (Sec. 3, Eq. ES-BGK) with parameter es_b, at the rate of
+    // the first time (tau_20); else SMRT.
     SMRT_D static void relax_coefficients(T (&v)[M], const T (&u)[3], T rho, T theta, T thm1, T o0,
-                                          const T *tauA, const T *tauB) {
+                                          const T *tauA, const T *tauB, int model = 0, T es_b = T(0)) {
         to_local<N>(v, u, theta, thm1);
         // a5: relax orders 2..N; order 0 is rho, order 1 is zero by definition of u
-        T s[KT];
-        static_for<KT>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
-        });
-        static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
+        if (model == 1) {
+            relax_es_divided<N, T>(v, rho, tauA[0], tauB[0], es_b);
+        } else {
+            T s[KT];
+            static_for<KT>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                s[k] = T(1) - rcp_tau<T>(tauA[k], tauB[k], rho);
+            });
+            static_for<N - 1>([&](auto Nn) { relax_order<N, decltype(Nn)::value + 2, T>(v, s); });
+        }
         // a6: back to the absolute frame: scale by theta^(|beta|/2), transform with T(u, theta)
         const T sq = theta * rsq(theta);
         T sp[N + 1];
@@ -584,7 +590,8 @@ struct Collide {
     // The whole collision: df (pre-collision deviations, library order) -> df (post-collision).
     // Returns false when rho or theta is not positive (or NaN).
     SMRT_D static bool collide(T (&f)[Q], const T (&wp)[NP + 1], const float (&wlo)[NP + 1], T c,
-                               float clo, const T *tauA, const T *tauB, unsigned key = 0u) {
+                               float clo, const T *tauA, const T *tauB, unsigned key = 0u, int model = 0,
+                               T es_b = T(0)) {
         if constexpr (Split) {
             bool finite = true;
             const bool ok = collide_split(
@@ -592,7 +599,7 @@ struct Collide {
                     finite &= (__float_as_uint(f[decltype(I)::value]) & 0x7f800000u) != 0x7f800000u;
                     return to_fixed(f[decltype(I)::value]);
                 },
-                [&](int i, T v) { f[i] = v; }, wp, wlo, c, clo, tauA, tauB, key);
+                [&](int i, T v) { f[i] = v; }, wp, wlo, c, clo, tauA, tauB, key, model, es_b);
             return ok && finite;
         } else {
             // a3: coefficients of the deviations; the full a has 1 more in slot 0, i.e. a_0 = rho
@@ -610,7 +617,7 @@ struct Collide {
             const T theta = T(1) + thm1;
             const bool ok = (rho > T(0)) && (theta > T(0));
             v[0] = rho;
-            relax_coefficients(v, u, rho, theta, thm1, rho, tauA, tauB);
+            relax_coefficients(v, u, rho, theta, thm1, rho, tauA, tauB, model, es_b);
             v[0] = rhom1;  // deviation from the coefficients of w_i
             T out[Q];
             rebuild<T>(v, c, wp, out);
@@ -649,7 +656,7 @@ struct Collide {
     template <class Pull, class Store>
     SMRT_D static bool collide_split(Pull &&pullq, Store &&store, const T (&wp)[NP + 1],
                                      const float (&wlo)[NP + 1], T c, float clo, const T *tauA,
-                                     const T *tauB, unsigned key) {
+                                     const T *tauB, unsigned key, int model = 0, T es_b = T(0)) {
         static_assert(std::is_same<T, float>::value, "the split precision stores floats");
         constexpr int px = mi_pos(1, 0, 0), py = mi_pos(0, 1, 0), pz = mi_pos(0, 0, 1);
         constexpr int pxx = mi_pos(2, 0, 0), pyy = mi_pos(0, 2, 0), pzz = mi_pos(0, 0, 2);
@@ -716,7 +723,7 @@ struct Collide {
         const T u[3] = {uf[0].hi, uf[1].hi, uf[2].hi};
         const bool ok = (rhof > T(0)) && (thetaf > T(0));
         // a4-a6 on the non-equilibrium part; orders 0 and 1 leave as zero
-        relax_coefficients(v, u, rhof, thetaf, thm1f, T(0), tauA, tauB);
+        relax_coefficients(v, u, rhof, thetaf, thm1f, T(0), tauA, tauB, model, es_b);
         // the post-collision coefficients: order-N equilibrium ta^eq_alpha = rho prod_k
         // G_k[alpha_k] (slot 0: rho - 1; G_k[j+1] = (u_k G_k[j] + (theta - 1) G_k[j-1]) / (j + 1))
         // plus the relaxed non-equilibrium part, then the monomial coefficients in xi,
@@ -928,7 +935,8 @@ __global__ void __launch_bounds__(128, kStepMinBlocks<Split>) step_box_kernel(St
         });
     });
     const bool ok = C::collide(f, a.wp, a.wlo, a.c, a.clo, tau_a<T>(a.inst[0]), tau_b<T>(a.inst[0]),
-                               mix32(unsigned(z * slab + y * row + x) ^ mix32(a.step)));
+                               mix32(unsigned(z * slab + y * row + x) ^ mix32(a.step)), a.inst[0].model,
+                               T(a.inst[0].es_b));
     if (!ok) atomicOr(a.health, 1u);
     const long long cell = z * slab + y * row + x;
     static_for<Lat::Q>([&](auto I) {
@@ -996,13 +1004,14 @@ SMRT_D void line_tile(const StepArgs<Lat, T> &a, const T *__restrict__ fin, T *_
     if constexpr (Split) {
         ok = C::collide_split([&](auto I) { return pull_split(decltype(I)::value, src_x(I)); },
                               [&](int i, T v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wlo, a.c,
-                              a.clo, tau_a<T>(in), tau_b<T>(in), mix32(unsigned(base + x) ^ mix32(step)));
+                              a.clo, tau_a<T>(in), tau_b<T>(in), mix32(unsigned(base + x) ^ mix32(step)),
+                              in.model, T(in.es_b));
         ok = ok && finite;
     } else {
         T f[Lat::Q];
         static_for<Lat::Q>([&](auto I) { f[decltype(I)::value] = pull(decltype(I)::value, src_x(I)); });
         ok = C::collide(f, a.wp, a.wlo, a.c, a.clo, tau_a<T>(in), tau_b<T>(in),
-                        mix32(unsigned(base + x) ^ mix32(step)));
+                        mix32(unsigned(base + x) ^ mix32(step)), in.model, T(in.es_b));
         static_for<Lat::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             fout[a.plane[i] + base + x] = f[i];
@@ -1151,7 +1160,7 @@ SMRT_D bool line_warp_staged(const StepArgs<Lat, float> &a, const float *__restr
     };
     const bool ok = C::collide_split(pullq, [&](int i, float v) { fout[a.plane[i] + base + x] = v; }, a.wp, a.wlo,
                                      a.c, a.clo, tau_a<float>(in), tau_b<float>(in),
-                                     mix32(unsigned(base + x) ^ mix32(step)));
+                                     mix32(unsigned(base + x) ^ mix32(step)), in.model, float(in.es_b));
     if (!(ok && finite)) atomicOr(a.health, 1u);
     return true;
 }

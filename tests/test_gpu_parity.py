@@ -284,3 +284,56 @@ def test_invalid_calls_are_rejected(lats):
         P.lb_init_lattice(_desc(d, (0, 0, 0)), 8, 2, 8, N=3)
     with pytest.raises(P.SmrtError):            # N = 4 needs degree 8
         P.lb_init_lattice(_desc(d, (0, 0, 0)), 8, 8, 8, N=4)
+
+
+# ---------------------------------------------------------------------------- ES-BGK
+@pytest.mark.parametrize("name,N,prec,tol", [("D3Q39", 3, "f64", 1e-12), ("D3Q39", 3, "f32", 2e-6),
+                                              ("D3Q103", 4, "f64", 1e-12), ("D3Q103", 4, "f32", 2e-6),
+                                              ("D3Q103", 4, "f32c64", 2e-6)])
+def test_es_bgk_box_steps_match_oracle(lats, name, N, prec, tol):
+    """The ES-BGK model (Sec. 3, Eq. ES-BGK, b = -1/2: Pr = 2/3) on the D3Q39 / D3Q103 kernels:
+    periodic box (two x-blocks and a ragged tail), 1 and 3 steps from a perturbed state."""
+    olat, d, idx = lats[name]
+    shape = (4, 5, 133)
+    model = OS.Model(olat, N, tau_ref=0.9, es_b=-0.5)
+    geom = OS.Geometry(shape=shape, shift=(1, 0, 0))
+    f0 = _perturbed_box(olat, N, shape).reshape(olat.q, *shape)
+    ctx = P.lb_init_lattice(_desc(d, (1, 0, 0)), shape[2], shape[1], shape[0], N=N, precision=prec)
+    P.lb_set_relaxation(ctx, _tau(model), True, 1.0)
+    P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, -0.5)
+    fa = upload(ctx, f0, idx)
+    fb = ctx.new_state()
+    if prec != "f64":
+        f0 = download(ctx, fa, idx).reshape(f0.shape)
+    for nsteps in (1, 3):
+        want = f0
+        for _ in range(nsteps):
+            want = OS.step(want, model, geom)
+        got = download(ctx, P.lb_step(ctx, upload(ctx, f0, idx), fb, nsteps), idx)
+        err = np.abs(got - want.reshape(olat.q, -1)).max() / np.abs(want).max()
+        assert err < tol * nsteps, (nsteps, err)
+    assert P.lb_poll_status(ctx)[0] == 0
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32c64", 3e-6)])
+def test_es_bgk_shock_steps_match_oracle(lats, prec, tol):
+    """ES-BGK on a Ma = 2 shock (D3Q103, N = 4, 300 cells, fixed ends; the split precision runs
+    the staged line kernel), 40 steps; the adjoint, written for SMRT, refuses such a context."""
+    olat, d, idx = lats["D3Q103"]
+    case, h, ctx = _shock_setup(olat, d, 4, 2.0, 300, 10.0, prec)
+    case.model.es_b = -0.5
+    P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, -0.5)
+    fa = upload(ctx, h, idx)
+    if prec != "f64":
+        h = download(ctx, fa, idx).reshape(h.shape)
+    fb = ctx.new_state()
+    for _ in range(40):
+        h = OS.step(h, case.model, case.geom)
+    got = download(ctx, P.lb_step(ctx, fa, fb, 40), idx)
+    assert np.abs(got - h.reshape(olat.q, -1)).max() / np.abs(h).max() < tol * 40
+    assert P.lb_poll_status(ctx)[0] == 0
+    if prec == "f64":
+        lam = torch.zeros(ctx.state_elems, dtype=torch.float64, device="cuda")
+        dtau = torch.zeros(7, dtype=torch.float64, device="cuda")
+        with pytest.raises(P.SmrtError):
+            P.lb_step_adjoint(ctx, fa, lam, torch.zeros_like(lam), dtau)

@@ -297,10 +297,10 @@ def test_es_target_matches_gaussian_integration(lats):
             assert abs(got[pos[beta], c] - want) < 1e-12 * max(1.0, abs(want)), beta
 
 
-def test_es_b_zero_is_bgk(lats):
+@pytest.mark.parametrize("name,N", [("D3Q729", 5), ("D3Q103", 4), ("D3Q39", 3)])
+def test_es_b_zero_is_bgk(lats, name, N):
     """ES-BGK with b = 0 is the BGK model: the regularised-BGK formula written without frames."""
-    lat = lats["D3Q729"]
-    N = 5
+    lat = lats[name]
     f, _ = _random_state(lat, N, eps=0.2)
     tau_c = 0.9
     model = S.Model(lat, N, tau_ref=tau_c, maxwell_law=False, es_b=0.0)
@@ -313,12 +313,12 @@ def test_es_b_zero_is_bgk(lats):
     np.testing.assert_allclose(S.collide(f, model), feq + (1.0 - 1.0 / (tau_c + 0.5)) * proj, atol=1e-13)
 
 
+@pytest.mark.parametrize("name,N", [("D3Q729", 5), ("D3Q103", 4), ("D3Q39", 3)])
 @pytest.mark.parametrize("b", [-0.5, 0.3])
-def test_es_prandtl_number_from_decay_rates(lats, b):
+def test_es_prandtl_number_from_decay_rates(lats, b, name, N):
     """Holway's model: Pr = 1/(1 - b) (2/3 at b = -1/2), read off the continuous relaxation
     times of a shear and a heat-flux mode measured from one collision."""
-    lat = lats["D3Q729"]
-    N = 5
+    lat = lats[name]
     model = S.Model(lat, N, tau_ref=1.3, maxwell_law=False, es_b=b)
     rng = np.random.default_rng(8)
     rates = {}
@@ -339,10 +339,11 @@ def test_es_prandtl_number_from_decay_rates(lats, b):
     assert abs(rates[(2, 0)] / rates[(3, 1)] - 1.0 / (1.0 - b)) < 1e-7
 
 
-def test_es_collision_conserves(lats):
-    lat = lats["D3Q729"]
-    f, _ = _random_state(lat, 5, eps=0.2)
-    h = S.collide(f, S.Model(lat, 5, tau_ref=0.7, es_b=-0.5))
+@pytest.mark.parametrize("name,N", [("D3Q729", 5), ("D3Q103", 4), ("D3Q39", 3)])
+def test_es_collision_conserves(lats, name, N):
+    lat = lats[name]
+    f, _ = _random_state(lat, N, eps=0.2)
+    h = S.collide(f, S.Model(lat, N, tau_ref=0.7, es_b=-0.5))
     for a, b in zip(S.conserved(f, lat), S.conserved(h, lat)):
         np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-14)
 
