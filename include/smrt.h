@@ -101,7 +101,7 @@ typedef struct {
  *   D3Q729 and D3Q4913, the tensor products of D1Q9-P1 and D1Q17-P1 (Sec. 4.2, Table 3:
  *   d = 9, degree 11; d = 17, degree 19), N = 4, 5:
  *     batched 1D lines (ny = nz = 1), frame shift along x only, LB_F64 or LB_F32; weights
- *     must factor as w_a w_b w_c with equal weights for +e and -e. No adjoint. The states
+ *     must factor as w_a w_b w_c with equal weights for +e and -e. The states
  *     passed to the stepping calls must start on 16-byte boundaries (LB_ERR_INVALID
  *     otherwise): the kernel stages population segments with the bulk-copy engine. When e
  *     lists the velocities in the library order (i = a + d b + d^2 c over the 1D order rest,
@@ -253,8 +253,11 @@ lb_status lb_moments(lb_ctx *ctx, const void *f, double *out, unsigned which_mas
  * times tau_c,nm. Arithmetic is double whatever the precision of f_t. Populations pulled from
  * beyond a fixed x end are constants (no gradient). The per-block gradient partials live in a
  * scratch array owned by the context; calls on one context must not overlap.
+ * Every set has adjoint kernels; on D3Q729 and D3Q4913 the projection of lam_next and the
+ * evaluation of the raw moments' adjoint factor over the axes as the forward step does
+ * (one thread per cell, 32-cell tiles, the per-tile gradient partials reduced in tile order).
  * Errors: LB_ERR_INVALID (null, lam_next overlapping lam_t, relaxation unset), LB_ERR_UNSUPPORTED
- * (a set without adjoint kernels, or an instance using the ES-BGK model), LB_ERR_CUDA. */
+ * (an instance using the ES-BGK model), LB_ERR_CUDA. */
 lb_status lb_step_adjoint(lb_ctx *ctx, const void *f_t, const double *lam_next, double *lam_t,
                           double *dtau);
 

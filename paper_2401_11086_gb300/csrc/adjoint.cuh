@@ -23,69 +23,10 @@
 
 namespace smrt {
 
-template <class Lat, int Nm>
-struct AdjMath {
-    static constexpr int Q = Lat::Q;
-    static constexpr int NP = Lat::NP;
+// The moment-space stages (independent of the velocity set).
+template <int Nm>
+struct AdjMoments {
     static constexpr int M = nmom(Nm);
-
-    // F1: Rc_g = c^|g| sum_i x_i e_i^g  (x in library order; pairs folded)
-    SMRT_HD static void raw(const double (&x)[Q], double c, double (&Rc)[M]) {
-        double S[NP], D[NP];
-        static_for<NP>([&](auto P) {
-            constexpr int p = decltype(P)::value;
-            S[p] = x[2 * p + 1] + x[2 * p + 2];
-            D[p] = x[2 * p + 1] - x[2 * p + 2];
-        });
-        double cp = 1.0;
-        double cpow[Nm + 1];
-        static_for<Nm + 1>([&](auto J) {
-            cpow[decltype(J)::value] = cp;
-            cp *= c;
-        });
-        static_for<M>([&](auto G) {
-            constexpr int g = decltype(G)::value;
-            constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-            constexpr bool even = ((g0 + g1 + g2) & 1) == 0;
-            double acc = (g == 0) ? x[0] : 0.0;
-            static_for<NP>([&](auto Pp) {
-                constexpr int p = decltype(Pp)::value;
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
-                if constexpr (m != 0) acc += double(m) * (even ? S[p] : D[p]);
-            });
-            Rc[g] = acc * cpow[mi_order(g)];
-        });
-    }
-
-    // F1': xb_i += sum_g c^|g| e_i^g Rcb_g
-    SMRT_HD static void raw_T(const double (&Rcb)[M], double c, double (&xb)[Q]) {
-        double cp = 1.0;
-        double sc[M];
-        double cpow[Nm + 1];
-        static_for<Nm + 1>([&](auto J) {
-            cpow[decltype(J)::value] = cp;
-            cp *= c;
-        });
-        static_for<M>([&](auto G) { sc[decltype(G)::value] = Rcb[decltype(G)::value] * cpow[mi_order(decltype(G)::value)]; });
-        xb[0] += sc[0];
-        static_for<NP>([&](auto Pp) {
-            constexpr int p = decltype(Pp)::value;
-            double ev = 0.0, od = 0.0;
-            static_for<M>([&](auto G) {
-                constexpr int g = decltype(G)::value;
-                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
-                if constexpr (m != 0) {
-                    if constexpr (((g0 + g1 + g2) & 1) == 0)
-                        ev += double(m) * sc[g];
-                    else
-                        od += double(m) * sc[g];
-                }
-            });
-            xb[2 * p + 1] += ev + od;
-            xb[2 * p + 2] += ev - od;
-        });
-    }
 
     // F3 (hdiv) / F7 (hfull) coefficient maps and their transposes
     template <bool Full>
@@ -284,6 +225,73 @@ struct AdjMath {
     }
 };
 
+// ... and the sums over the populations of a velocity set with compile-time vectors.
+template <class Lat, int Nm>
+struct AdjMath : AdjMoments<Nm> {
+    static constexpr int Q = Lat::Q;
+    static constexpr int NP = Lat::NP;
+    static constexpr int M = nmom(Nm);
+
+    // F1: Rc_g = c^|g| sum_i x_i e_i^g  (x in library order; pairs folded)
+    SMRT_HD static void raw(const double (&x)[Q], double c, double (&Rc)[M]) {
+        double S[NP], D[NP];
+        static_for<NP>([&](auto P) {
+            constexpr int p = decltype(P)::value;
+            S[p] = x[2 * p + 1] + x[2 * p + 2];
+            D[p] = x[2 * p + 1] - x[2 * p + 2];
+        });
+        double cp = 1.0;
+        double cpow[Nm + 1];
+        static_for<Nm + 1>([&](auto J) {
+            cpow[decltype(J)::value] = cp;
+            cp *= c;
+        });
+        static_for<M>([&](auto G) {
+            constexpr int g = decltype(G)::value;
+            constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+            constexpr bool even = ((g0 + g1 + g2) & 1) == 0;
+            double acc = (g == 0) ? x[0] : 0.0;
+            static_for<NP>([&](auto Pp) {
+                constexpr int p = decltype(Pp)::value;
+                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                if constexpr (m != 0) acc += double(m) * (even ? S[p] : D[p]);
+            });
+            Rc[g] = acc * cpow[mi_order(g)];
+        });
+    }
+
+    // F1': xb_i += sum_g c^|g| e_i^g Rcb_g
+    SMRT_HD static void raw_T(const double (&Rcb)[M], double c, double (&xb)[Q]) {
+        double cp = 1.0;
+        double sc[M];
+        double cpow[Nm + 1];
+        static_for<Nm + 1>([&](auto J) {
+            cpow[decltype(J)::value] = cp;
+            cp *= c;
+        });
+        static_for<M>([&](auto G) { sc[decltype(G)::value] = Rcb[decltype(G)::value] * cpow[mi_order(decltype(G)::value)]; });
+        xb[0] += sc[0];
+        static_for<NP>([&](auto Pp) {
+            constexpr int p = decltype(Pp)::value;
+            double ev = 0.0, od = 0.0;
+            static_for<M>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
+                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                if constexpr (m != 0) {
+                    if constexpr (((g0 + g1 + g2) & 1) == 0)
+                        ev += double(m) * sc[g];
+                    else
+                        od += double(m) * sc[g];
+                }
+            });
+            xb[2 * p + 1] += ev + od;
+            xb[2 * p + 2] += ev - od;
+        });
+    }
+
+};
+
 // Conserved moments from the raw moments (F2) and the transpose of F2 (onto Rcb).
 template <int M>
 struct Conserved {
@@ -313,21 +321,20 @@ struct Conserved {
     }
 };
 
-// Per-cell VJP of the collision: given pre-collision deviations f and lam = dL/d out,
-// fb = (d out / d f)^T lam and taub_k = sum over the cell of lam . d out / d tau_c,k.
-// dAdt / dBdt: derivatives of the per-slot A, B with respect to tau_c (see top).
-template <class Lat, int N>
-SMRT_HD void collide_vjp(const double (&f)[Lat::Q], const double (&lam)[Lat::Q], double c,
-                         const double (&wp)[Lat::NP + 1], const double *tauA, const double *tauB,
-                         double dAdt, double dBdt, double (&fb)[Lat::Q], double (&taub)[ntau(N)]) {
-    using AM = AdjMath<Lat, N>;
+// Moment-space part of the collision's VJP, common to every velocity set: Rc_g = c^|g| sum_i
+// df_i e_i^g (the pre-collision raw moments) and Lc_g = c^|g| sum_i w_i lam_i e_i^g (the
+// projection of the weighted adjoint of the rebuilt populations) in; Rcb (out, overwritten) =
+// the adjoint of Rc, so that fb_i = sum_g c^|g| e_i^g Rcb_g; taub_k += sum over the cell of
+// lam . d out / d tau_c,k. dAdt / dBdt: derivatives of the per-slot A, B with respect to tau_c
+// (see top).
+template <int N>
+SMRT_HD void moment_vjp(const double (&Rc)[nmom(N)], const double (&Lc)[nmom(N)], const double *tauA,
+                        const double *tauB, double dAdt, double dBdt, double (&Rcb)[nmom(N)],
+                        double (&taub)[ntau(N)]) {
+    using AM = AdjMoments<N>;
     constexpr int M = nmom(N);
-    constexpr int Q = Lat::Q;
-    constexpr int NP = Lat::NP;
     constexpr int KT = ntau(N);
     // ---- forward recompute
-    double Rc[M];
-    AM::raw(f, c, Rc);
     Conserved<M> cs;
     cs.from_raw(Rc);
     const double rho = cs.rho, th = cs.th, t1 = cs.thm1;
@@ -395,15 +402,7 @@ SMRT_HD void collide_vjp(const double (&f)[Lat::Q], const double (&lam)[Lat::Q],
     AM::template pass<1>(q1, Gp[1], q2);
 
     // ---- reverse
-    double wl[Q];
-    wl[0] = wp[0] * lam[0];
-    static_for<NP>([&](auto Pp) {
-        constexpr int p = decltype(Pp)::value;
-        wl[2 * p + 1] = wp[p + 1] * lam[2 * p + 1];
-        wl[2 * p + 2] = wp[p + 1] * lam[2 * p + 2];
-    });
-    double Lc[M], tapb[M];
-    AM::raw(wl, c, Lc);
+    double tapb[M];
     static_for<M>([&](auto A) { tapb[decltype(A)::value] = 0.0; });
     AM::template hmap<true>(Lc, tapb);  // F7': tapb_a = sum_g hfull(a, g) Lc_g
     double rhob = tapb[0];               // ta'_0 := rho - 1 after the transform
@@ -496,25 +495,46 @@ SMRT_HD void collide_vjp(const double (&f)[Lat::Q], const double (&lam)[Lat::Q],
     // F3'
     rhob += tab[0];
     tab[0] = 0.0;
-    double Rcb[M];
     static_for<M>([&](auto A) { Rcb[decltype(A)::value] = 0.0; });
     AM::template hmap_T<false>(tab, Rcb);
     // F2', F1'
     cs.transpose(rhob, ub, tb, Rcb);
+}
+
+// Per-cell VJP of the collision: given pre-collision deviations f and lam = dL/d out,
+// fb = (d out / d f)^T lam and taub_k = sum over the cell of lam . d out / d tau_c,k.
+template <class Lat, int N>
+SMRT_HD void collide_vjp(const double (&f)[Lat::Q], const double (&lam)[Lat::Q], double c,
+                         const double (&wp)[Lat::NP + 1], const double *tauA, const double *tauB,
+                         double dAdt, double dBdt, double (&fb)[Lat::Q], double (&taub)[ntau(N)]) {
+    using AM = AdjMath<Lat, N>;
+    constexpr int M = nmom(N);
+    constexpr int Q = Lat::Q;
+    constexpr int NP = Lat::NP;
+    double Rc[M], Lc[M], Rcb[M];
+    AM::raw(f, c, Rc);
+    double wl[Q];
+    wl[0] = wp[0] * lam[0];
+    static_for<NP>([&](auto Pp) {
+        constexpr int p = decltype(Pp)::value;
+        wl[2 * p + 1] = wp[p + 1] * lam[2 * p + 1];
+        wl[2 * p + 2] = wp[p + 1] * lam[2 * p + 2];
+    });
+    AM::raw(wl, c, Lc);
+    moment_vjp<N>(Rc, Lc, tauA, tauB, dAdt, dBdt, Rcb, taub);
     static_for<Q>([&](auto I) { fb[decltype(I)::value] = 0.0; });
     AM::raw_T(Rcb, c, fb);
 }
 
-// Per-cell VJP of the moments rho, u (physical), theta, q of lb_moments: given their adjoints
-// (qb[3], ub_out[3]), fb = (d moments / d f)^T (.). Uses the order-3 local coefficients.
-template <class Lat, int N>
-SMRT_HD void moments_vjp(const double (&f)[Lat::Q], double c, double rhob_out, const double (&ub_out)[3],
-                         double thb_out, const double (&qb)[3], double (&fb)[Lat::Q]) {
-    constexpr int Nm = N < 3 ? 3 : N;
-    using AM = AdjMath<Lat, Nm>;
+// Moment-space part of the VJP of the moments rho, u (physical), theta, q of lb_moments: Rc (the
+// raw moments, c-scaled, |g| <= max(N, 3)) in; Rcb (out, overwritten) their adjoint given the
+// moments' adjoints, so that fb_i = sum_g c^|g| e_i^g Rcb_g. Uses the order-3 local
+// coefficients.
+template <int Nm>
+SMRT_HD void moments_vjp_m(const double (&Rc)[nmom(Nm)], double rhob_out, const double (&ub_out)[3],
+                           double thb_out, const double (&qb)[3], double (&Rcb)[nmom(Nm)]) {
+    using AM = AdjMoments<Nm>;
     constexpr int M = nmom(Nm);
-    double Rc[M];
-    AM::raw(f, c, Rc);
     Conserved<M> cs;
     cs.from_raw(Rc);
     const double th = cs.th, t1 = cs.thm1;
@@ -563,10 +583,22 @@ SMRT_HD void moments_vjp(const double (&f)[Lat::Q], double c, double rhob_out, c
     }
     double rhob = rhob_out + tab[0];
     tab[0] = 0.0;
-    double Rcb[M];
     static_for<M>([&](auto A) { Rcb[decltype(A)::value] = 0.0; });
     AM::template hmap_T<false>(tab, Rcb);
     cs.transpose(rhob, ub, tb, Rcb);
+}
+
+// Per-cell VJP of the moments rho, u (physical), theta, q of lb_moments: given their adjoints
+// (qb[3], ub_out[3]), fb = (d moments / d f)^T (.).
+template <class Lat, int N>
+SMRT_HD void moments_vjp(const double (&f)[Lat::Q], double c, double rhob_out, const double (&ub_out)[3],
+                         double thb_out, const double (&qb)[3], double (&fb)[Lat::Q]) {
+    constexpr int Nm = N < 3 ? 3 : N;
+    using AM = AdjMath<Lat, Nm>;
+    constexpr int M = nmom(Nm);
+    double Rc[M], Rcb[M];
+    AM::raw(f, c, Rc);
+    moments_vjp_m<Nm>(Rc, rhob_out, ub_out, thb_out, qb, Rcb);
     static_for<Lat::Q>([&](auto I) { fb[decltype(I)::value] = 0.0; });
     AM::raw_T(Rcb, c, fb);
 }

@@ -193,7 +193,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
             c->ks = prec == LB_F64 ? kernels_d3q729_p0(N) : (prec == LB_F32 ? kernels_d3q729_p1(N) : nullptr);
         else
             c->ks = prec == LB_F64 ? kernels_d3q4913_p0(N) : (prec == LB_F32 ? kernels_d3q4913_p1(N) : nullptr);
-        c->as = nullptr;
+        c->as = t729 ? adjoints_d3q729(N, prec) : adjoints_d3q4913(N, prec);
         // batched 1D lines only, shifted along x only
         if (grid->ny != 1 || grid->nz != 1 || lat->shift[1] != 0 || lat->shift[2] != 0) c->ks = nullptr;
     } else if (match_set<D3Q39>(lat, c->perm)) {

@@ -495,6 +495,8 @@ struct AdjointSet {
 };
 const AdjointSet *adjoints_d3q39(int N, int precision);
 const AdjointSet *adjoints_d3q103(int N, int precision);
+const AdjointSet *adjoints_d3q729(int N, int precision);
+const AdjointSet *adjoints_d3q4913(int N, int precision);
 
 template <class Lat, class T>
 AdjArgs<Lat, T> make_adj_args(const CtxView &v, const void *f) {
@@ -554,6 +556,44 @@ template <class Lat, int N, int P>
 const AdjointSet *adjoint_set() {
     using T = typename std::conditional<P == 0, double, float>::type;
     static const AdjointSet as = {&launch_adj_step<Lat, N, T>, &launch_adj_moments<Lat, N, T>};
+    return &as;
+}
+
+}  // namespace smrt
+
+#include "tensor_adjoint.cuh"
+
+namespace smrt {
+
+// Tensor-product sets: 32-cell tiles, one thread per cell (tensor_adjoint.cuh).
+template <class L1, int N, class T>
+cudaError_t tp_launch_adj_step(const CtxView &v, const void *f, const double *lam_next, double *lam_t,
+                               double *partials, double *dtau) {
+    const TPArgs<T> a = make_tp_args<T>(v, f, nullptr);
+    if (v.fixedx)
+        tp_adjoint_step_kernel<L1, N, T, true><<<v.ntiles, 32, 0, v.stream>>>(a, lam_next, lam_t, partials);
+    else
+        tp_adjoint_step_kernel<L1, N, T, false><<<v.ntiles, 32, 0, v.stream>>>(a, lam_next, lam_t, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_partials_kernel<<<1, 32, 0, v.stream>>>(partials, (long long)v.ntiles, ntau(N), dtau);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_adj_moments(const CtxView &v, const void *f, const double *gbar, unsigned mask, double *lam) {
+    const TPArgs<T> a = make_tp_args<T>(v, f, nullptr);
+    if (v.fixedx)
+        tp_adjoint_moments_kernel<L1, N, T, true><<<v.ntiles, 32, 0, v.stream>>>(a, gbar, mask, lam, v.ncells);
+    else
+        tp_adjoint_moments_kernel<L1, N, T, false><<<v.ntiles, 32, 0, v.stream>>>(a, gbar, mask, lam, v.ncells);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, int P>
+const AdjointSet *tp_adjoint_set() {
+    using T = typename std::conditional<P == 0, double, float>::type;
+    static const AdjointSet as = {&tp_launch_adj_step<L1, N, T>, &tp_launch_adj_moments<L1, N, T>};
     return &as;
 }
 

@@ -188,3 +188,119 @@ def test_differentiable_shock_ma5_full_size():
     L32, tau32 = loss_of(ctx32, taus0, upload(ctx32, h0, idx))
     L32.backward()
     np.testing.assert_allclose(tau32.grad.numpy(), g, rtol=5e-3, atol=1e-4 * gmax)
+
+
+# ------------------------------------------------------------------ the paper's D3Q729 set
+def _tp_setup(Ma, nx, prec="f64", theta1=None):
+    from paper_2401_11086_gb300 import shocks
+    olat = OL.d3q729()
+    d = P.lb_lattice_named("D3Q729")
+    idx = lib_from_oracle(olat, d)
+    th1 = shocks.TABLE3_THETA1[Ma] if theta1 is None else theta1
+    case = OK.shock_case(olat, 5, Ma, nx, theta1=th1)
+    st = case.states
+    h0 = OK.initial_state(case, *[synthetic.step_blend(nx, st[k + "1"], st[k + "2"])
+                                  for k in ("rho", "u", "theta")])
+    left, right = P.lb_rankine_hugoniot(Ma, theta1=th1)
+    ctx = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree, (case.k, 0, 0)), nx, N=5,
+                            precision=prec, bc_x=1)
+    taus = OA.model_taus(case.model)
+    P.lb_set_relaxation(ctx, taus, True, 1.0, left, right)
+    return olat, d, idx, case, h0, ctx, taus
+
+
+@pytest.mark.parametrize("Ma", [1.5, 3.0, 5.0])
+def test_tp_step_adjoint_satisfies_the_adjoint_identity(Ma):
+    """lb_step_adjoint on D3Q729, N = 5, FP64 (the paper's configuration, Table 3 rows; 40 cells,
+    a 32-cell tile and a ragged one, fixed ends): for random directions dh, <lam^t, dh> equals
+    <lam^{t+1}, J dh> with J dh the oracle's complex-step derivative of one step, to 1e-11;
+    two of the directions are confined to the cells next to either end. dtau equals the
+    oracle's complex-step derivative in each relaxation time."""
+    olat, d, idx, case, h0, ctx, taus = _tp_setup(Ma, 40)
+    rng = np.random.default_rng(int(Ma * 10))
+    h = h0 * (1 + 0.02 * rng.standard_normal(h0.shape))
+    lam_next = rng.standard_normal(h.shape)
+    lt = torch.full((ctx.state_elems,), np.nan, dtype=torch.float64, device="cuda")
+    dtau = torch.zeros(len(taus), dtype=torch.float64, device="cuda")
+    P.lb_step_adjoint(ctx, upload(ctx, h, idx), _plain_up(ctx, lam_next, idx), lt, dtau)
+    got = _plain_down(ctx, lt, idx).reshape(h.shape)
+    assert np.isfinite(got).all()
+    hcs = 1e-30
+    dirs = [rng.standard_normal(h.shape) for _ in range(2)]
+    for lo, hi in ((0, 6), (34, 40)):
+        v = np.zeros(h.shape)
+        v[..., lo:hi] = rng.standard_normal(h[..., lo:hi].shape)
+        dirs.append(v)
+    for v in dirs:
+        jd = OS.step(h.astype(np.complex128) + 1j * hcs * v, case.model, case.geom).imag / hcs
+        want = np.sum(lam_next * jd)
+        assert abs(np.sum(got * v) - want) < 1e-11 * np.sum(np.abs(lam_next * jd)), want
+    model = case.model
+    for p, k in enumerate(OA.tau_keys(5)):
+        tc = np.asarray(taus, dtype=np.complex128)
+        tc[p] += 1j * hcs
+        mc = OA.model_with_taus(model, tc)
+        jd = OS.step(h.astype(np.complex128), mc, case.geom).imag / hcs
+        want = np.sum(lam_next * jd)
+        assert abs(dtau[p].item() - want) < 1e-10 * max(1.0, np.sum(np.abs(lam_next * jd))), (k, want)
+    assert abs(dtau[OA.tau_keys(5).index((2, 1))].item()) < 1e-10
+
+
+def test_tp_moments_adjoint_satisfies_the_adjoint_identity():
+    """lb_moments_adjoint on D3Q729 (N = 5): <lam, dh> = <gbar, d moments(h; dh)> for the loss
+    moments rho, theta, q_x, the derivative by complex step of the oracle's macroscopic()."""
+    olat, d, idx, case, h0, ctx, taus = _tp_setup(3.0, 40)
+    rng = np.random.default_rng(31)
+    h = h0 * (1 + 0.02 * rng.standard_normal(h0.shape))
+    mask = P.LB_MOM_RHO | P.LB_MOM_THETA | P.LB_MOM_Q
+    st = upload(ctx, h, idx)
+    m = P.lb_moments(ctx, st, mask)
+    gbar = torch.from_numpy(rng.standard_normal(tuple(m.shape))).cuda()
+    lam = torch.full((ctx.state_elems,), np.nan, dtype=torch.float64, device="cuda")
+    P.lb_moments_adjoint(ctx, st, gbar, mask, lam)
+    got = _plain_down(ctx, lam, idx).reshape(h.shape)
+    g = gbar.cpu().numpy()
+    hcs = 1e-30
+    for _ in range(3):
+        v = rng.standard_normal(h.shape)
+        mc = OS.macroscopic(h.astype(np.complex128) + 1j * hcs * v, case.model, case.geom)
+        dm = np.stack([mc["rho"].imag, mc["theta"].imag, mc["q"][0].imag, mc["q"][1].imag, mc["q"][2].imag]) / hcs
+        want = np.sum(g * dm)
+        assert abs(np.sum(got * v) - want) < 1e-11 * np.sum(np.abs(g * dm)), want
+
+
+def test_tp_relaxation_run_gradient_matches_finite_differences():
+    """Checkpointed autograd run on the paper's configuration (D3Q729, N = 5, FP64, Table 3's
+    Ma = 3 row, 100 cells, step start): 200 steps, checkpoint every 50, loss on rho, theta, q_x
+    against a run at relaxation times perturbed by +-20 %. The gradient in every time matches
+    central differences (h = 1e-4 relative) to 1e-4, and d L / d tau_21 (bulk) vanishes."""
+    olat, d, idx, case, h0, ctx, taus_ref = _tp_setup(3.0, 100)
+    taus0 = taus_ref * synthetic.perturbed(np.ones(len(taus_ref)), 0.2, seed=5)
+    h0s = upload(ctx, h0, idx)
+    with torch.no_grad():
+        tgt = relaxation_run(ctx, torch.tensor(taus_ref, dtype=torch.float64), h0s, 200, checkpoint_every=50)
+
+    def loss_of(tau_np):
+        tau = torch.tensor(tau_np, dtype=torch.float64, requires_grad=True)
+        out = relaxation_run(ctx, tau, h0s, 200, checkpoint_every=50)
+        L = ((out[0] - tgt[0]) ** 2 + (out[1] - tgt[1]) ** 2 + (out[2] - tgt[2]) ** 2).sum()
+        return L, tau
+
+    L, tau = loss_of(taus0)
+    L.backward()
+    g = tau.grad.numpy()
+    assert P.lb_poll_status(ctx)[0] == 0
+    gmax = np.abs(g).max()
+    keys = OA.tau_keys(5)
+    for p, k in enumerate(keys):
+        if k == (2, 1):
+            continue
+        vals = []
+        for sgn in (1, -1):
+            t = taus0.copy()
+            t[p] += sgn * 1e-4 * taus0[p]
+            with torch.no_grad():
+                vals.append(loss_of(t)[0].item())
+        fd = (vals[0] - vals[1]) / (2e-4 * taus0[p])
+        assert abs(fd - g[p]) <= 1e-4 * abs(fd) + 1e-7 * gmax, (k, fd, g[p])
+    assert abs(g[keys.index((2, 1))]) < 1e-6 * gmax
