@@ -37,7 +37,8 @@ Q = 39
 N_ORDER = 3
 METRIC = "GLUPSxQ (cell-velocity updates/s) and % HBM roofline"
 UNIT = "G cell-velocity updates/s"
-KERNEL_SOURCES = ["core.cuh", "kernels.cuh", "lattices.cuh", "dispatch.h"]
+# the device code of the box and batched-line kernels (launch set-up excluded)
+KERNEL_SOURCES = ["core.cuh", "kernels.cuh", "lattices.cuh"]
 PROFILE = os.path.join(ROOT, "profiles", "collide_stream_d3q39_f32_box.txt")
 PROFILE_BATCHED = os.path.join(ROOT, "profiles", "collide_stream_d3q103_n4_batched.txt")
 
@@ -173,6 +174,30 @@ print(json.dumps({{"rate": b ** 3 * lat.q * {steps} / dt, "seconds": dt}}))
     if res.returncode != 0:
         raise RuntimeError(f"oracle baseline failed: {res.stderr[-2000:]}")
     return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_rate_all_cores(block: int, steps: int, warmup: int = 1) -> dict:
+    """The same oracle sample run as one process per host core at once (independent samples,
+    single-threaded BLAS each): the aggregate rate of the host's cores, with their count."""
+    ncores = os.cpu_count() or 1
+    code = f"""
+import sys, json
+sys.path.insert(0, {ROOT!r})
+import bench
+print(json.dumps(bench.oracle_sample_rate({block}, {steps}, {warmup})))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True, env=env) for _ in range(ncores)]
+    rates = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"oracle baseline failed: {err[-2000:]}")
+        rates.append(json.loads(out.strip().splitlines()[-1])["rate"])
+    return {"rate": float(sum(rates)), "cores": ncores, "seconds": time.perf_counter() - t0}
 
 
 def run_reference(args, rank: int) -> None:
@@ -342,9 +367,10 @@ def run_batched(args, world: int, rank: int, local: int) -> None:
 TP_FP64_FLOP_PER_CELL = 14949.0
 FP64_PEAK_GFLOPS = 1250.0
 # warp instructions per cell-step of the split-precision D3Q103, N = 4 staged line kernel on the
-# 64 batched shocks (ncu smsp__inst_executed.sum of one launch / cells), and the issue rate of a
-# GB300 (4 schedulers per SM, 152 SMs, 2070 MHz, one warp instruction per clock each)
-BATCHED_WARP_INST_PER_CELL = 501.9
+# 64 batched shocks (ncu smsp__inst_executed.sum of one launch / cells: 499.9 for the persistent
+# form, 501.9 for one plain launch per step), and the issue rate of a GB300 (4 schedulers per SM,
+# 152 SMs, 2070 MHz, one warp instruction per clock each)
+BATCHED_WARP_INST_PER_CELL = 499.9
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 
 
@@ -646,7 +672,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence", "cfg4"],
                     help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
@@ -743,22 +769,62 @@ def main():
     rate, total_ms = job_rate(cells * Q * K, total_ms, dist)
     value = rate / 1e9
 
-    # end to end through the public API with host buffers: every step copies the state in from
-    # pinned host memory, steps once, and copies the new state back
+    # end to end through the public API with host buffers: every step copies its state in from
+    # pinned host memory, steps once, and copies the new state back. Steps are independent
+    # batches, pipelined as a user streaming them would: two device state pairs, the copy in on
+    # one stream, the step on the context's stream, the copy out on a third, so that one step's
+    # copy in runs while the previous one's copy out does (the host link is full duplex).
     state_bytes = ctx.state_elems * 4
-    host_in = torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True)
-    host_out = torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True)
-    host_in.copy_(cur)
     E = args.e2e_steps
+    host_in = [torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    host_out = [torch.empty(ctx.state_elems, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    for h in host_in:
+        h.copy_(cur)
+    # a context of its own on a non-default stream: work on the legacy default stream would
+    # serialise with the copy streams
+    s_comp, s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ctx_e = P.lb_init_lattice(P.LatticeDesc(d.e, d.w, d.c, d.degree), n, n, n, N=N_ORDER,
+                              precision="f32", stream=s_comp)
+    P.lb_set_relaxation(ctx_e, [r * tau20 for r in tau_table()], True, 1.0)
+    dev_in, dev_out = [fa, ctx_e.new_state()], [fb, ctx_e.new_state()]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_step = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def pipeline(nsteps):
+        for k in range(nsteps):
+            b = k & 1
+            if k >= 2:
+                s_in.wait_event(ev_step[b])        # the step two back has read dev_in[b]
+            with torch.cuda.stream(s_in):
+                dev_in[b].copy_(host_in[b], non_blocking=True)
+            ev_in[b].record(s_in)
+            s_comp.wait_event(ev_in[b])
+            if k >= 2:
+                s_comp.wait_event(ev_out[b])       # the copy out two back has read dev_out[b]
+            res = P.lb_step(ctx_e, dev_in[b], dev_out[b], 1)
+            ev_step[b].record(s_comp)
+            s_out.wait_event(ev_step[b])
+            with torch.cuda.stream(s_out):
+                host_out[b].copy_(res, non_blocking=True)
+            ev_out[b].record(s_out)
+        s_comp.wait_event(ev_out[(nsteps - 1) & 1])
+        if nsteps > 1:
+            s_comp.wait_event(ev_out[nsteps & 1])
+
+    pipeline(E)                                 # untimed: the first passes over fresh pinned pages
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(E):
-        fa.copy_(host_in, non_blocking=True)
-        res = P.lb_step(ctx, fa, fb, 1)
-        host_out.copy_(res, non_blocking=True)
-    e1.record(stream)
+    e0.record(s_comp)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    pipeline(E)
+    e1.record(s_comp)
     torch.cuda.synchronize()
+    st_e, flags_e = P.lb_poll_status(ctx_e)
+    if st_e != 0:
+        raise SystemExit(f"end-to-end run: health word reports status {st_e} (flags {flags_e})")
+    ctx_e.close()
     e2e_ms = e0.elapsed_time(e1) / E
     e2e_value = world * cells * Q / (e2e_ms * 1e-3) / 1e9
 
@@ -773,9 +839,13 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_sample_rate(32, 20)
+        ra = oracle_sample_rate_all_cores(24, 10)
         cpu = {"value": r["rate"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "32^3 corner block of the 256^3 Taylor-Green box stepped as its own "
-                         "periodic box, 20 FP64 oracle steps, single-threaded BLAS"}
+                         "periodic box, 20 FP64 oracle steps, single-threaded BLAS",
+               "all_cores": {"value": ra["rate"] / 1e9, "unit": UNIT, "cores": ra["cores"],
+                             "sample": "one 24^3 corner block, 10 oracle steps, per host core, "
+                                       "all at once (independent samples, one BLAS thread each)"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -790,7 +860,9 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": kern_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
+                "d2h_bytes_per_step": state_bytes, "steps": E,
+                "pipeline": "independent steps, double-buffered: copy in, step and copy out on "
+                            "three streams"},
         "gpu_launches": K,
         "clocks": clk,
     }
