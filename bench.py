@@ -374,29 +374,36 @@ BATCHED_WARP_INST_PER_CELL = 499.9
 ISSUE_PEAK_GINST = 4 * 152 * 2.07
 
 
-def table3_instances(rank: int, count: int = 512, length: int = 0):
-    """The D3Q729 workload of one rank: count shocks cycling over Table 3's rows (Ma 3, 1.5, 5
-    with their theta1), lengths 100..400 cells drawn with seed 11086 + rank, or all `length`
-    cells when given (a single shock is then the paper's Ma = 3 run)."""
+def table3_instances(rank: int, count: int = 512, length: int = 0, lattice: str = "D3Q729"):
+    """The Table 3 workload of one rank: count shocks cycling over the D3Q729 rows (Ma 3, 1.5,
+    5 with their theta1), or all on the D3Q4913 row (Ma 7), lengths 100..400 cells drawn with
+    seed 11086 + rank, or all `length` cells when given (a single shock is then the paper's
+    run of that row)."""
     import numpy as np
     from paper_2401_11086_gb300 import shocks
-    machs = [(3.0, 1.5, 5.0)[j % 3] for j in range(count)]
+    if lattice == "D3Q4913":
+        machs = [7.0] * count
+    else:
+        machs = [(3.0, 1.5, 5.0)[j % 3] for j in range(count)]
     if length > 0:
         lengths = np.full(count, length)
     else:
         lengths = np.random.default_rng(11086 + rank).integers(100, 401, count)
-    return machs, lengths, [shocks.TABLE3_THETA1[m] for m in machs]
+    th = {**shocks.TABLE3_THETA1, **shocks.TABLE3_THETA1_D1Q17}
+    return machs, lengths, [th[m] for m in machs]
 
 
-def oracle_table3_rate(steps: int) -> dict:
-    """FP64 oracle on one Table 3 shock (Ma = 3, 100 cells, D3Q729, N = 5), single-threaded."""
+def oracle_table3_rate(steps: int, lattice: str = "D3Q729") -> dict:
+    """FP64 oracle on one Table 3 shock (Ma = 3 on D3Q729, Ma = 7 on D3Q4913; 100 cells,
+    N = 5), single-threaded."""
+    mk, Ma, th1, q = {"D3Q729": ("d3q729", 3.0, 0.333, 729), "D3Q4913": ("d3q4913", 7.0, 0.071, 4913)}[lattice]
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import synthetic
 from oracle import lattice as L, shock as K, smrt as S
-lat = L.d3q729()
-case = K.shock_case(lat, 5, 3.0, 100, theta1=0.333)
+lat = L.{mk}()
+case = K.shock_case(lat, 5, {Ma}, 100, theta1={th1})
 st = case.states
 h = K.initial_state(case, *[synthetic.step_blend(100, st[k + "1"], st[k + "2"]) for k in ("rho", "u", "theta")])
 h = S.step(h, case.model, case.geom)
@@ -404,7 +411,7 @@ t0 = time.perf_counter()
 for _ in range({steps}):
     h = S.step(h, case.model, case.geom)
 dt = time.perf_counter() - t0
-print(json.dumps({{"rate": 100 * 729 * {steps} / dt, "seconds": dt}}))
+print(json.dumps({{"rate": 100 * {q} * {steps} / dt, "seconds": dt}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
@@ -425,14 +432,18 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    machs, lengths, theta1 = table3_instances(rank, args.instances, args.length)
-    d = P.lb_lattice_named("D3Q729")
+    machs, lengths, theta1 = table3_instances(rank, args.instances, args.length, args.lattice)
+    d = P.lb_lattice_named(args.lattice)
     stream = torch.cuda.current_stream()
     prec = args.precision
     ctx, f0, _ = shocks.setup_batch(d, 5, machs, lengths, precision=prec, width=0.0, theta1=theta1,
                                     stream=stream)
     if args.es_b is not None:          # the ES-BGK model (Sec. 3) instead of SMRT
         P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, args.es_b)
+    if args.tensor_cores:              # the projection's x-row sums on the tensor cores
+        s0 = P.lb_get_schedule(ctx)
+        P.lb_set_schedule(ctx, s0["tile_width"] if s0["tile_width"] > 1 else 64, s0["blocks_per_sm"],
+                          s0["persistent"], tensor_cores=1)
     sched = P.lb_get_schedule(ctx)   # the library's choice for this size
     fa, fb = f0, ctx.new_state()
     cur = P.lb_step(ctx, fa, fb, args.warmup)
@@ -442,7 +453,7 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
         dist.barrier()
     K = args.steps
     cells = int(sum(lengths))
-    q = 729
+    q = d.q
     elem = 8 if prec == "f64" else 4
     # states that fit in the 129 MB L2 are flushed (256 MB write) before every timed step
     small = 2 * q * elem * cells < 129e6
@@ -475,7 +486,7 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
             "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)",
             "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": kern_ms,
             "note": "issue-bound: the HBM fraction says how far from the memory roofline"}
-    if prec == "f64":
+    if prec == "f64" and args.lattice == "D3Q729":
         # the FP64 pipe bounds the double kernel: its double-precision operations per
         # cell-step (ncu instruction counts, an FMA counted as two) against the nominal rate
         gflop = TP_FP64_FLOP_PER_CELL * cells / (kern_ms * 1e-3) / 1e9
@@ -485,13 +496,16 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
                 "hbm_frac": achieved / peak}
     cpu = None
     if not args.no_cpu_baseline:
-        r = oracle_table3_rate(40)
+        nst = 40 if args.lattice == "D3Q729" else 6
+        r = oracle_table3_rate(nst, args.lattice)
+        row = "Ma = 3, 100 cells, D3Q729" if args.lattice == "D3Q729" else "Ma = 7, 100 cells, D3Q4913"
         cpu = {"value": r["rate"] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one Table 3 shock (Ma = 3, 100 cells, D3Q729, N = 5), 40 FP64 oracle steps"}
+               "sample": f"one Table 3 shock ({row}, N = 5), {nst} FP64 oracle steps"}
     line = {"metric": METRIC, "value": rate / 1e9, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": f"table3_d3q729_n5_{prec}" + ("" if args.es_b is None else "_es_bgk"),
+            "config": {"workload": f"table3_{args.lattice.lower()}_n5_{prec}" + ("" if args.es_b is None else "_es_bgk")
+                                   + ("_tensor_core_xrows" if args.tensor_cores else ""),
                        "collision": "SMRT" if args.es_b is None else f"ES-BGK b={args.es_b}",
                        "instances_per_gpu": len(machs),
                        "cells_per_gpu": cells, "velocities": q, "hermite_order": 5,
@@ -684,6 +698,10 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
                     help="table3 workload only")
     ap.add_argument("--instances", type=int, default=512, help="table3 workload: number of shocks")
+    ap.add_argument("--lattice", default="D3Q729", choices=["D3Q729", "D3Q4913"],
+                    help="table3 workload: the D3Q729 rows (Ma 1.5/3/5) or the D3Q4913 row (Ma 7)")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="table3 workload, f32: the projection's x-row sums on the tensor cores")
     ap.add_argument("--length", type=int, default=0,
                     help="table3 workload: cells per shock (0: 100..400 by seed)")
     args = ap.parse_args()

@@ -189,22 +189,30 @@ lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
  * persistent = 1: lb_step runs all its steps in one cooperative launch of blocks_per_sm
  * blocks per SM (0 = as many as fit), tiles spread over the blocks, a grid-wide barrier between
  * steps (its wait is bounded: on timeout the health word gets LB_HEALTH_TIMEOUT and the
- * launch ends); persistent = 0: one launch per step. ms_per_step: measured by lb_autotune. */
+ * launch ends); persistent = 0: one launch per step. tensor_cores = 1 (LB_F32 D3Q729 / D3Q4913
+ * lines with fixed ends, tile widths 32/64/128): the x-row sums of the projection (Eq. an, the
+ * first of its three factored passes) run as warp-wide TF32 matrix products on the tensor
+ * cores, with each population split into two TF32 parts and each power e^j into two, three
+ * products per tile, for single-precision accuracy; 0: on the CUDA cores. ms_per_step: measured
+ * by lb_autotune. */
 typedef struct {
     int tile_width;
     int blocks_per_sm;
     int persistent;
+    int tensor_cores;
     double ms_per_step;
 } lb_schedule;
 
 /* lb_set_schedule / lb_get_schedule -- apply or read a schedule (a periodic box accepts only
- * {128, 0, 0}). Setting a new tile width rebuilds the context's tile table (synchronises).
- * Errors: LB_ERR_INVALID, LB_ERR_UNSUPPORTED (persistent kernel cannot be resident), LB_ERR_CUDA. */
+ * {128, 0, 0, 0}). Setting a new tile width rebuilds the context's tile table (synchronises).
+ * Errors: LB_ERR_INVALID, LB_ERR_UNSUPPORTED (persistent kernel cannot be resident; tensor_cores
+ * on any other context), LB_ERR_CUDA. */
 lb_status lb_set_schedule(lb_ctx *ctx, const lb_schedule *schedule);
 lb_status lb_get_schedule(const lb_ctx *ctx, lb_schedule *schedule);
 
 /* lb_autotune -- time every candidate schedule (tile widths 32/64/128, and 1 on D3Q729; one
- * launch per step or persistent with 1, 2, 4 or all resident blocks per SM) for trial_steps steps on the states
+ * launch per step or persistent with 1, 2, 4 or all resident blocks per SM; x-row sums on the
+ * CUDA cores and, where allowed, the tensor cores) for trial_steps steps on the states
  * f_a / f_b (which it ADVANCES: pass copies), apply the fastest and return it in *best with
  * its ms_per_step. Synchronises. Errors: as lb_step, LB_ERR_CUDA. */
 lb_status lb_autotune(lb_ctx *ctx, void *f_a, void *f_b, int trial_steps, lb_schedule *best);

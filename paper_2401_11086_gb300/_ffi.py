@@ -31,7 +31,7 @@ class LbState(ctypes.Structure):
 
 class LbSchedule(ctypes.Structure):
     _fields_ = [("tile_width", c_int), ("blocks_per_sm", c_int), ("persistent", c_int),
-                ("ms_per_step", c_double)]
+                ("tensor_cores", c_int), ("ms_per_step", c_double)]
 
 
 # name -> (restype, argtypes); every symbol include/smrt.h declares

@@ -261,11 +261,12 @@ def lb_moments_adjoint(ctx: Context, f, gbar, mask: int, lam):
 
 def _sched_dict(s: LbSchedule) -> dict:
     return {"tile_width": s.tile_width, "blocks_per_sm": s.blocks_per_sm,
-            "persistent": s.persistent, "ms_per_step": s.ms_per_step}
+            "persistent": s.persistent, "tensor_cores": s.tensor_cores, "ms_per_step": s.ms_per_step}
 
 
-def lb_set_schedule(ctx: Context, tile_width: int = 128, blocks_per_sm: int = 0, persistent: int = 0):
-    s = LbSchedule(int(tile_width), int(blocks_per_sm), int(persistent), 0.0)
+def lb_set_schedule(ctx: Context, tile_width: int = 128, blocks_per_sm: int = 0, persistent: int = 0,
+                    tensor_cores: int = 0):
+    s = LbSchedule(int(tile_width), int(blocks_per_sm), int(persistent), int(tensor_cores), 0.0)
     _check(_ffi.lib().lb_set_schedule(ctx.handle, byref(s)), "lb_set_schedule")
 
 

@@ -43,7 +43,7 @@ def tuned_schedule(ctx: api.Context, f, lengths, trial_steps: int = 20, path: st
     db = _load(path)
     if key in db and not retune:
         s = db[key]
-        api.lb_set_schedule(ctx, s["tile_width"], s["blocks_per_sm"], s["persistent"])
+        api.lb_set_schedule(ctx, s["tile_width"], s["blocks_per_sm"], s["persistent"], s.get("tensor_cores", 0))
         return s
     fa, fb = f.clone(), ctx.new_state()
     best = api.lb_autotune(ctx, fa, fb, trial_steps)

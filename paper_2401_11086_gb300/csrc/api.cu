@@ -282,6 +282,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     c->sched.tile_width = line ? width0 : kTile;
     c->sched.blocks_per_sm = 0;
     c->sched.persistent = 0;
+    c->sched.tensor_cores = 0;
     c->sched.ms_per_step = 0.0;
     c->ncells = ncells;
     c->stride = (ncells + 63) / 64 * 64;  // planes start on 256-byte boundaries (float)
@@ -557,6 +558,10 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
     if (s->tile_width != 32 && s->tile_width != 64 && s->tile_width != 128 && !cell_blocks) return LB_ERR_INVALID;
     if (cell_blocks && (c->kind != 2 || s->persistent)) return LB_ERR_UNSUPPORTED;
     if (s->blocks_per_sm < 0 || (s->persistent != 0 && s->persistent != 1)) return LB_ERR_INVALID;
+    if (s->tensor_cores != 0 && s->tensor_cores != 1) return LB_ERR_INVALID;
+    // tensor-core x-rows: the warp-staged kernels of float tensor-product lines with fixed ends
+    if (s->tensor_cores && (c->kind < 2 || c->prec != LB_F32 || !c->view.line || !c->view.fixedx || cell_blocks))
+        return LB_ERR_UNSUPPORTED;
     if (!c->view.line) {  // the box kernel has one fixed launch shape
         if (s->persistent || s->tile_width != kTile) return LB_ERR_UNSUPPORTED;
         c->sched = *s;
@@ -575,6 +580,7 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
         c->view.tile_width = s->tile_width;
     }
     c->sched = *s;
+    c->view.tensor_cores = s->tensor_cores;
     if (c->sched.persistent && c->ks->occupancy(c->view) < 1) {
         c->sched.persistent = 0;
         return LB_ERR_UNSUPPORTED;
@@ -594,22 +600,26 @@ extern "C" lb_status lb_autotune(lb_ctx *c, void *fa, void *fb, int trial_steps,
     std::vector<lb_schedule> cand;
     const int widths[4] = {32, 64, 128, 1};
     const int nwidths = c->view.line ? (c->kind == 2 ? 4 : 3) : 1;
-    for (int wi = 0; wi < nwidths; ++wi) {
-        const int width = c->view.line ? widths[wi] : kTile;
-        cand.push_back(lb_schedule{width, 0, 0, 0.0});  // one launch per step
-        if (!c->view.line || width == 1) continue;
-        const lb_schedule probe{width, 0, 1, 0.0};
-        if (lb_set_schedule(c, &probe) != LB_OK) continue;
-        const int occ = c->ks->occupancy(c->view);
-        const int opts[4] = {1, 2, 4, occ};
-        for (int bps : opts) {
-            if (bps < 1 || bps > occ) continue;
-            bool dup = false;
-            for (const lb_schedule &q : cand)
-                dup = dup || (q.tile_width == width && q.persistent && q.blocks_per_sm == bps);
-            if (!dup) cand.push_back(lb_schedule{width, bps, 1, 0.0});  // persistent launch
+    // x-row sums on the CUDA cores, and on the tensor cores where the context allows it
+    const int ntc = (c->kind >= 2 && c->prec == LB_F32 && c->view.line && c->view.fixedx) ? 2 : 1;
+    for (int tc = 0; tc < ntc; ++tc)
+        for (int wi = 0; wi < nwidths; ++wi) {
+            const int width = c->view.line ? widths[wi] : kTile;
+            if (tc && width == 1) continue;
+            cand.push_back(lb_schedule{width, 0, 0, tc, 0.0});  // one launch per step
+            if (!c->view.line || width == 1) continue;
+            const lb_schedule probe{width, 0, 1, tc, 0.0};
+            if (lb_set_schedule(c, &probe) != LB_OK) continue;
+            const int occ = c->ks->occupancy(c->view);
+            const int opts[4] = {1, 2, 4, occ};
+            for (int bps : opts) {
+                if (bps < 1 || bps > occ) continue;
+                bool dup = false;
+                for (const lb_schedule &q : cand)
+                    dup = dup || (q.tile_width == width && q.persistent && q.blocks_per_sm == bps && q.tensor_cores == tc);
+                if (!dup) cand.push_back(lb_schedule{width, bps, 1, tc, 0.0});  // persistent launch
+            }
         }
-    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return LB_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -663,7 +673,8 @@ extern "C" lb_status lb_step_graph(lb_ctx *c, void *fa, void *fb, int nsteps) {
     if (!c->view.line || persistent_grid(c) < 1) return LB_ERR_UNSUPPORTED;
     const bool same = c->graph && c->graph_fa == fa && c->graph_fb == fb && c->graph_steps == nsteps &&
                       c->graph_sched.tile_width == c->sched.tile_width &&
-                      c->graph_sched.blocks_per_sm == c->sched.blocks_per_sm;
+                      c->graph_sched.blocks_per_sm == c->sched.blocks_per_sm &&
+                      c->graph_sched.tensor_cores == c->sched.tensor_cores;
     if (!same) {
         if (c->graph) {
             cudaGraphExecDestroy(c->graph);

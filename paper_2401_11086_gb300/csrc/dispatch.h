@@ -43,6 +43,8 @@ struct CtxView {
     long long stride;
     double w1[kMaxQ1];
     int plane_identity;  // 1: library population i is caller plane i (tensor-map staging applies)
+    int tensor_cores;    // 1: float tensor-product lines with fixed ends sum their x-rows on the
+                         // tensor cores (lb_schedule::tensor_cores)
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
@@ -388,6 +390,14 @@ cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
     TPMaps maps;
     std::memset(&maps, 0, sizeof(maps));
     a.tma = tp_encode_map<L1, T>(v, fin, &maps.src) ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (v.fixedx && v.tensor_cores) {
+            const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true, true>, L1, T>();
+            if (e != cudaSuccess) return e;
+            tp_step_line_warp<L1, N, T, true, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
+            return cudaGetLastError();
+        }
+    }
     if (v.fixedx) {
         const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true>, L1, T>();
         if (e != cudaSuccess) return e;
@@ -440,6 +450,14 @@ cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nstep
     cfg.numAttrs = 1;
     const int ntiles = v.ntiles;
     unsigned *bar = v.bar;
+    if constexpr (std::is_same<T, float>::value) {
+        if (v.fixedx && v.tensor_cores) {
+            const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true, true>, L1, T>();
+            if (e != cudaSuccess) return e;
+            return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true, true>, a, nsteps, ntiles, bar,
+                                      maps);
+        }
+    }
     if (v.fixedx) {
         const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
         if (e != cudaSuccess) return e;
@@ -455,6 +473,15 @@ int tp_persistent_occupancy(const CtxView &v) {
     int n = 0;
     const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
     cudaError_t e;
+    if constexpr (std::is_same<T, float>::value) {
+        if (v.fixedx && v.tensor_cores) {
+            e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true, true>, L1, T>();
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, true, true>,
+                                                                  v.tile_width, smem);
+            return e == cudaSuccess ? n : 0;
+        }
+    }
     if (v.fixedx) {
         e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
         if (e == cudaSuccess)

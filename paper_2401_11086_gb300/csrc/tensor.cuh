@@ -668,12 +668,118 @@ struct TPWarpStage {
     SMRT_HD static size_t bytes(int threads) { return size_t(threads / 32) * kWarpBytes; }
 };
 
+// ------------------------------------------------------------------ x-row sums on tensor cores
+// The x-row sums of one stage, g_j = sum_a f_a e_a^j for each of the warp's 32 cells and the
+// stage's one or two x-rows, as one warp-wide matrix product: rows (x-row, cell), columns
+// j = 0..7 (those above N are zero), inner index a = 1 .. d - 1 in k-steps of 8; the rest
+// velocity (e_0 = 0) adds to g_0 only and seeds the accumulator. mma.sync m16n8k8 with TF32
+// operands and FP32 accumulation; single-precision accuracy from the operand split of Ootomo &
+// Yokota (2022, "Recovering single precision accuracy from Tensor Cores while surpassing the
+// FP32 theoretical peak performance"): f = f_hi + f_lo with f_hi = f rounded to TF32 and f_lo
+// the remainder rounded to TF32 (each rounding within 2^-11 relative), e^j = E_hi + E_lo
+// likewise and exactly (e^j <= 9^5 has at most 16 significant bits, E_lo at most 5), and
+// g = f_lo E_hi + f_hi E_lo + f_hi E_hi; the dropped f_lo E_lo and the rounding of f_lo are
+// each below 2^-22 of |f| e^j.
+// m16n8k8 TF32 fragments, lane = 4 r + q: A rows r and r + 8, columns q and q + 4; B rows
+// (inner index) q and q + 4, column r; C rows r and r + 8, columns 2q and 2q + 1.
+template <class L1, int N>
+struct TPTensorRows {
+    static constexpr int KS = (L1::Q1 - 1) / 8;  // k-steps over a = 1 .. d - 1
+    static_assert((L1::Q1 - 1) % 8 == 0 && N + 1 <= 8, "k-steps of 8 velocities, j <= 7");
+    static constexpr int kPitch = 10;            // floats per (x-row, cell) row of the scratch
+    unsigned bhi[KS][2], blo[KS][2];             // B fragments, e_a^j split in two
+    int off[KS][2];                              // a SEG - e_a for the lane's two columns
+    int r, q;
+
+    SMRT_D static unsigned tf32(float x) {
+        unsigned u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+        return u;
+    }
+    SMRT_D static void mma(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+        asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+            "{%8, %9}, {%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+
+    // seg: elements per staged row
+    SMRT_D void init(int lane, int seg) {
+        r = lane >> 2;
+        q = lane & 3;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int av = 8 * ks + q + 4 * h + 1;
+                int e = 0;
+                static_for<L1::Q1>([&](auto A) {
+                    if (decltype(A)::value == av) e = e1<L1>(decltype(A)::value);
+                });
+                off[ks][h] = av * seg - e;
+                float pw = r <= N ? 1.f : 0.f;  // e^r, exact in float
+                for (int j = 0; j < r; ++j) pw *= float(e);
+                const unsigned hi = tf32(pw);
+                bhi[ks][h] = hi;
+                blo[ks][h] = tf32(pw - __uint_as_float(hi));
+            }
+    }
+
+    // g[x][j], x < NR, for the lane's cell: the pull of x-row x by velocity a of cell c sits at
+    // bs[x grp + a SEG + tb0 + c - e_a]. Every lane calls it. The first NR 32 kPitch floats of bs
+    // serve as scratch to hand each cell its row sums, so bs is overwritten.
+    template <int NR>
+    SMRT_D void rows(float *bs, int grp, int tb0, int lane, float (&g)[NR][N + 1]) const {
+        float acc[NR][2][4];
+#pragma unroll
+        for (int x = 0; x < NR; ++x)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const float *p = bs + x * grp + tb0 + 16 * mt + r;
+                float(&d)[4] = acc[x][mt];
+                d[0] = q == 0 ? p[0] : 0.f;  // the rest velocity: column j = 0
+                d[1] = 0.f;
+                d[2] = q == 0 ? p[8] : 0.f;
+                d[3] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    const float v[4] = {p[off[ks][0]], p[off[ks][0] + 8], p[off[ks][1]], p[off[ks][1] + 8]};
+                    unsigned ahi[4], alo[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ahi[i] = tf32(v[i]);
+                        alo[i] = tf32(v[i] - __uint_as_float(ahi[i]));
+                    }
+                    mma(d, alo, bhi[ks][0], bhi[ks][1]);
+                    mma(d, ahi, blo[ks][0], blo[ks][1]);
+                    mma(d, ahi, bhi[ks][0], bhi[ks][1]);
+                }
+            }
+        __syncwarp();  // every lane holds its operands: the buffer is free
+        if (2 * q <= N) {
+#pragma unroll
+            for (int x = 0; x < NR; ++x)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    float *o = bs + (x * 32 + 16 * mt + r) * kPitch + 2 * q;
+                    *reinterpret_cast<float2 *>(o) = make_float2(acc[x][mt][0], acc[x][mt][1]);
+                    *reinterpret_cast<float2 *>(o + 8 * kPitch) = make_float2(acc[x][mt][2], acc[x][mt][3]);
+                }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int x = 0; x < NR; ++x)
+            static_for<N + 1>([&](auto J) { g[x][decltype(J)::value] = bs[(x * 32 + lane) * kPitch + decltype(J)::value]; });
+    }
+};
+
 // One warp tile of the step. buf, bar: the warp's stage buffers and mbarriers; bit b of parity
 // is the parity of buffer b's next fill, bit b of pending says that fill is in flight. All 32
 // lanes call it (lanes past the line's end idle). Returns false, with LB_HEALTH_TIMEOUT in
 // the health word, when a fill did not land within the bounded wait.
 // tm: tensor map of fin (one box per x-row group), or null to copy plane by plane.
-template <class L1, int N, class T, bool FixedX, bool Coherent>
+// TC (float only): the x-row sums of every stage on the tensor cores (TPTensorRows).
+template <class L1, int N, class T, bool FixedX, bool Coherent, bool TC = false>
 SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *__restrict__ fin,
                          T *__restrict__ fout, int tile_index, T *buf, unsigned long long *bar, unsigned &parity,
                          unsigned &pending, const CUtensorMap *tm) {
@@ -736,6 +842,12 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
             const int t = x - e1<L1>(av) - kx;
             if (t < 0 || t >= L) beyond |= 1u << av;
         });
+    static_assert(!TC || std::is_same<T, float>::value, "tensor-core x-rows are TF32 (float states)");
+    TPTensorRows<L1, N> tc;
+    if constexpr (TC) {
+        static_assert(2 * 32 * TPTensorRows<L1, N>::kPitch <= S::kStage, "scratch fits a stage buffer");
+        tc.init(lane, SEG);
+    }
     for (int st = 0; st < NS; ++st) issue(st);
     T R[C::M];
     static_for<C::M>([&](auto G) { R[decltype(G)::value] = T(0); });
@@ -779,6 +891,21 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
                 });
                 fence_async_shared();  // own slots rewritten: before the buffer's next fill
             }
+        }
+        if constexpr (TC) {
+            __syncwarp();  // the rewritten slots are operands of other lanes
+            if (p == 0) {
+                float g[1][N + 1];
+                tc.template rows<1>(bs, S::kGrp, tb - lane, lane, g);
+                if (active) C::yrest(g[0], h);
+            } else {
+                float g[2][N + 1];
+                tc.template rows<2>(bs, S::kGrp, tb - lane, lane, g);
+                if (active) C::ypair_pw(g[0], g[1], s.pw[2 * p - 1], h);
+            }
+            if (active && p == NP1) C::zfold_pw(h, s.pw[cz], R);
+            fence_async_shared();  // scratch written and read: before the buffer's next fill
+        } else if (active) {
             const T *r0 = bs + tb;
             auto rowp = [&](auto A) -> T {
                 constexpr int av = decltype(A)::value;
@@ -847,7 +974,7 @@ SMRT_D void tp_warp_setup(unsigned char *dyn, unsigned long long *&bar, T *&buf)
 // One step: warp w of block b takes the 32-cell tile b * (blockDim / 32) + w.
 // maps: tensor maps of the two states, used when a.tma is set (and the dynamic shared memory
 // is 128-byte aligned, as the boxes need).
-template <class L1, int N, class T, bool FixedX>
+template <class L1, int N, class T, bool FixedX, bool TC = false>
 __global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T> s;
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -859,12 +986,12 @@ __global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles
     if (t >= ntiles) return;
     unsigned parity = 0u, pending = 0u;
     const CUtensorMap *tm = (a.tma && (smem_addr(dyn) & 127u) == 0u) ? &maps.src : nullptr;
-    tp_warp_tile<L1, N, T, FixedX, false>(a, s, a.fin, a.fout, t, buf, bar, parity, pending, tm);
+    tp_warp_tile<L1, N, T, FixedX, false, TC>(a, s, a.fin, a.fout, t, buf, bar, parity, pending, tm);
 }
 
 // All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh); the
 // warps stride over the 32-cell tiles.
-template <class L1, int N, class T, bool FixedX>
+template <class L1, int N, class T, bool FixedX, bool TC = false>
 __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a, int nsteps, int ntiles,
                                                                     unsigned *barg, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T> s;
@@ -886,7 +1013,7 @@ __global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a,
     for (int st = 0; st < nsteps; ++st) {
         const CUtensorMap *tm = use_tma ? (src == a.fin ? &maps.src : &maps.dst) : nullptr;
         for (int t = blockIdx.x * wpb + int(threadIdx.x >> 5); t < ntiles; t += gridDim.x * wpb)
-            if (!tp_warp_tile<L1, N, T, FixedX, true>(a, s, src, dst, t, buf, bar, parity, pending, tm)) {
+            if (!tp_warp_tile<L1, N, T, FixedX, true, TC>(a, s, src, dst, t, buf, bar, parity, pending, tm)) {
                 failed = 1;
                 break;
             }

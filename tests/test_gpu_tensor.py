@@ -450,3 +450,72 @@ def test_mixed_mach_batch_graph_replay_against_golden(lat, prec, tol_rho, tol_q)
         assert np.abs(m[4][s] / th - 1).max() < tol_rho, (j, machs[j])
         assert np.abs(m[5][s] - q).max() / np.abs(q).max() < tol_q, (j, machs[j])
     ctx.close()
+
+
+# ------------------------------------------------------------------ x-row sums on tensor cores
+@pytest.mark.parametrize("sched", [(64, 0, 0), (32, 0, 0), (128, 2, 1)])
+def test_tensor_core_xrows_table3_f32(lat, sched):
+    """FP32 with the x-row sums of the projection on the tensor cores (TF32 operands split in
+    two, three products): the three Table 3 rows in one batch from the step start, 8 steps,
+    vs the oracle at the FP32 bound of 2e-6 per step, and vs the CUDA-core x-rows."""
+    olat, d, idx = lat
+    ctx, params, cases, hs = _batch(olat, d, 5, "f32")
+    fa = _upload_batch(ctx, d, idx, hs)
+    nsteps = 8
+    P.lb_set_schedule(ctx, *sched, tensor_cores=0)
+    ref = P.lb_step(ctx, fa.clone(), ctx.new_state(), nsteps).clone()
+    P.lb_set_schedule(ctx, *sched, tensor_cores=1)
+    assert P.lb_get_schedule(ctx)["tensor_cores"] == 1
+    out = P.lb_step(ctx, fa, ctx.new_state(), nsteps)
+    assert P.lb_poll_status(ctx)[0] == 0
+    got = _download_batch(ctx, d, idx, out, LENGTHS)
+    for j, (case, h) in enumerate(zip(cases, hs)):
+        for _ in range(nsteps):
+            h = OS.step(h, case.model, case.geom)
+        want = h.reshape(olat.q, -1)
+        assert np.abs(got[j] - want).max() / np.abs(want).max() < 2e-6 * nsteps, (j, MACHS[j])
+    scale = ref.abs().max()
+    assert 0 < ((out - ref).abs().max() / scale).item() < 2e-6 * nsteps
+
+
+def test_tensor_core_xrows_ma7_d3q4913_f32(lat17):
+    """D3Q4913 (two k-steps of 8 velocities per x-row), Table 3's Ma = 7 row, FP32 with the
+    tensor-core x-rows, two shocks of 40 and 70 cells, 6 steps, plain and persistent launches
+    and a graph replay vs the oracle."""
+    olat, d, idx = lat17
+    lengths = [40, 70]
+    ctx, _, params = shocks.setup_batch(d, 5, [7.0, 7.0], lengths, precision="f32", width=0.0,
+                                        theta1=[0.071, 0.071])
+    cases, hs = zip(*[_ma7_case(olat, 5, L) for L in lengths])
+    f0 = _upload_batch(ctx, d, idx, hs)
+    nsteps = 6
+    wants = []
+    for case, h in zip(cases, hs):
+        for _ in range(nsteps):
+            h = OS.step(h, case.model, case.geom)
+        wants.append(h.reshape(olat.q, -1))
+    for mode, sched in [("step", (64, 0, 0)), ("step", (64, 1, 1)), ("graph", (32, 2, 1))]:
+        P.lb_set_schedule(ctx, *sched, tensor_cores=1)
+        fa, fb = f0.clone(), ctx.new_state()
+        out = P.lb_step_graph(ctx, fa, fb, nsteps) if mode == "graph" else P.lb_step(ctx, fa, fb, nsteps)
+        assert P.lb_poll_status(ctx)[0] == 0
+        got = _download_batch(ctx, d, idx, out, lengths)
+        for j, want in enumerate(wants):
+            assert np.abs(got[j] - want).max() / np.abs(want).max() < 2e-6 * nsteps, (mode, sched, j)
+
+
+def test_tensor_core_xrows_refused_where_not_built(lat):
+    """tensor_cores applies to float tensor-product lines with fixed ends only."""
+    olat, d, idx = lat
+    ctx64, _, _ = shocks.setup_batch(d, 5, [3.0], [40], precision="f64", width=0.0, theta1=[0.333])
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(ctx64, 64, 0, 0, tensor_cores=1)
+    ctx32, _, _ = shocks.setup_batch(d, 5, [3.0], [40], precision="f32", width=0.0, theta1=[0.333])
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(ctx32, 1, 0, 0, tensor_cores=1)   # one block per cell
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(ctx32, 64, 0, 0, tensor_cores=2)
+    P.lb_set_schedule(ctx32, 64, 0, 0, tensor_cores=1)
+    per = P.lb_init_lattice(_desc(d, (2, 0, 0)), 40, N=5, precision="f32")
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(per, 64, 0, 0, tensor_cores=1)  # periodic line
