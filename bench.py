@@ -200,6 +200,40 @@ print(json.dumps(bench.oracle_sample_rate({block}, {steps}, {warmup})))
     return {"rate": float(sum(rates)), "cores": ncores, "seconds": time.perf_counter() - t0}
 
 
+# The other workloads, each timed by its own bench.py run after the box on the same GPU (one
+# GPU only), reported in the box line under "secondary": the 64 batched shocks on D3Q103 in the
+# split precision, the 512 Table 3 shocks on D3Q729 in FP32, and the mixed-Mach batch (Ma 1.2 to
+# 7 on D3Q729 / D3Q4913) as one graph replay of 1000 steps per set.
+SECONDARY_WORKLOADS = [
+    ["--workload", "batched", "--steps", "200", "--warmup", "5"],
+    ["--workload", "table3", "--precision", "f32", "--steps", "100", "--warmup", "5"],
+    ["--workload", "cfg4", "--steps", "1000", "--warmup", "3"],
+]
+
+
+def run_secondary(extra: list, timeout: float = 600.0) -> dict:
+    """One other workload's bench.py line, condensed: its own CUDA-event timing, roofline and
+    clocks, run as a child process (no oracle baseline)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), *extra, "--no-cpu-baseline", "--no-secondary"]
+    out = {"args": " ".join(extra)}
+    try:
+        res = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        out["error"] = f"no result within {timeout:.0f} s"
+        return out
+    lines = [x for x in res.stdout.splitlines() if x.startswith("{")]
+    if res.returncode != 0 or not lines:
+        out["error"] = (res.stderr or res.stdout)[-400:]
+        return out
+    d = json.loads(lines[-1])
+    roof = d.get("roofline") or {}
+    out.update({"workload": d["config"]["workload"], "value": d["value"], "unit": d["unit"],
+                "ms_per_step": d["ms_per_step"], "steps": d["steps"], "dtype": d["dtype"],
+                "roofline": {k: roof.get(k) for k in ("bound", "achieved", "peak", "unit", "frac")},
+                "clocks": d.get("clocks")})
+    return out
+
+
 def run_reference(args, rank: int) -> None:
     if rank != 0:
         return
@@ -688,6 +722,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="box workload: skip the other workloads' runs reported under 'secondary'")
     ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence", "cfg4"],
                     help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
                          "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5; convergence: the "
@@ -854,6 +890,12 @@ def main():
     if rank != 0:
         ctx.close()
         return
+    secondary = None
+    if world == 1 and not args.no_secondary:
+        ctx.close()                              # the children get the GPU's memory
+        del cur, other, fa, fb, dev_in, dev_out, host_in, host_out
+        torch.cuda.empty_cache()
+        secondary = [run_secondary(a) for a in SECONDARY_WORKLOADS]
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_sample_rate(32, 20)
@@ -884,8 +926,11 @@ def main():
         "gpu_launches": K,
         "clocks": clk,
     }
+    if secondary is not None:
+        line["secondary"] = secondary
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if secondary is None:
+        ctx.close()
     if dist:
         dist.destroy_process_group()
 
