@@ -207,7 +207,7 @@ print(json.dumps(bench.oracle_sample_rate({block}, {steps}, {warmup})))
 SECONDARY_WORKLOADS = [
     ["--workload", "batched", "--steps", "200", "--warmup", "5"],
     ["--workload", "table3", "--precision", "f32", "--steps", "100", "--warmup", "5"],
-    ["--workload", "cfg4", "--steps", "1000", "--warmup", "3"],
+    ["--workload", "mixed_mach", "--steps", "1000", "--warmup", "3"],
 ]
 
 
@@ -550,7 +550,7 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     print(json.dumps(line), flush=True)
 
 
-def run_cfg4(args, world: int, rank: int, local: int) -> None:
+def run_mixed_mach(args, world: int, rank: int, local: int) -> None:
     """The batched configuration as specified: 64 shocks with Ma ~ U[1.2, 7] and lengths from
     {512, ..., 8192} (seed 11086 + rank), each run for K steps by one persistent launch captured
     in a CUDA graph (lb_step_graph), launch schedule from the autotuner. The degree-9 set holds
@@ -724,10 +724,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="box workload: skip the other workloads' runs reported under 'secondary'")
-    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence", "cfg4"],
+    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence", "mixed_mach"],
                     help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
                          "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5; convergence: the "
-                         "Appendix B study; cfg4: 64 shocks with Ma in [1.2, 7] on D3Q729 / "
+                         "Appendix B study; mixed_mach: 64 shocks with Ma in [1.2, 7] on D3Q729 / "
                          "D3Q4913, K steps in one graph-captured persistent launch per set")
     ap.add_argument("--es-b", type=float, default=None,
                     help="table3 workload: run the ES-BGK model with this b instead of SMRT")
@@ -753,8 +753,8 @@ def main():
     if args.impl == "ours" and args.workload == "table3":
         run_table3(args, world, rank, local)
         return
-    if args.impl == "ours" and args.workload == "cfg4":
-        run_cfg4(args, world, rank, local)
+    if args.impl == "ours" and args.workload == "mixed_mach":
+        run_mixed_mach(args, world, rank, local)
         return
     if args.impl == "ours" and args.workload == "convergence":
         run_convergence(args, rank, local)
