@@ -181,7 +181,8 @@ lb_status lb_fill_equilibrium(lb_ctx *ctx, void *f, const double *rho, const dou
 lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 
 /* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128;
- * on D3Q729 and D3Q4913 each warp of the block takes its own 32-cell tile; on D3Q729 the value
+ * on D3Q729 and D3Q4913 a block of tile_width / 32 warps steps a tile of tile_width cells whose
+ * pulls it stages once for all its warps, one 32-cell row per warp; on D3Q729 the value
  * 1 selects one block per cell -- its populations in shared memory, the factored sums spread
  * over the block -- which lb_init_lattice picks for problems of at most 48 (LB_F64) or 32 (LB_F32)
  * cells per SM, and
@@ -190,7 +191,7 @@ lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
  * blocks per SM (0 = as many as fit), tiles spread over the blocks, a grid-wide barrier between
  * steps (its wait is bounded: on timeout the health word gets LB_HEALTH_TIMEOUT and the
  * launch ends); persistent = 0: one launch per step. tensor_cores = 1 (LB_F32 D3Q729 / D3Q4913
- * lines with fixed ends, tile widths 32/64/128): the x-row sums of the projection (Eq. an, the
+ * lines with fixed ends, tile width 32): the x-row sums of the projection (Eq. an, the
  * first of its three factored passes) run as warp-wide TF32 matrix products on the tensor
  * cores, with each population split into two TF32 parts and each power e^j into two, three
  * products per tile, for single-precision accuracy; 0: on the CUDA cores. ms_per_step: measured

@@ -52,13 +52,15 @@ struct lb_ctx {
     // device tables owned by the context
     InstanceInfo *d_inst;
     int2 *d_tiles;
+    int2 *d_btiles;      // tensor-product lines: block tiles of the step kernels (tile_width cells)
     int *d_plane;        // tensor-product sets: caller plane of each library population
     void *d_ghosts;
     double *d_ghostsd;
     double *d_states;
     unsigned *d_health;  // [0] health flags, [1..3] grid barrier and step counter
     double *d_partials;  // per-block relaxation-time gradients of lb_step_adjoint
-    long long max_tiles; // tile capacity (32-cell tiles) of d_tiles and d_partials
+    long long max_tiles; // tile capacity (32-cell tiles) of d_tiles, d_btiles and d_partials
+    int btile_width;     // cells per block tile in d_btiles
     lb_schedule sched;
     int num_sms;
     // cached graph of the persistent launch (lb_step_graph)
@@ -147,6 +149,7 @@ void free_tables(lb_ctx *c) {
     if (!c) return;
     cudaFree(c->d_inst);
     cudaFree(c->d_tiles);
+    cudaFree(c->d_btiles);
     cudaFree(c->d_plane);
     cudaFree(c->d_ghosts);
     cudaFree(c->d_ghostsd);
@@ -274,9 +277,11 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         in.kx = k0;
         ncells += line ? (size_t)in.nx : (size_t)grid->nx * grid->ny * grid->nz;
     }
-    // tensor-product contexts keep 32-cell tiles (one per warp); their tile width is the block
-    // size, 64 by default
-    const int width0 = tensor ? 64 : kTile;
+    // tensor-product contexts keep a table of 32-cell tiles (the moments, fill and adjoint
+    // kernels) and step in block tiles of the schedule's width. Default widths, as measured:
+    // float states stage best in 128-cell tiles; double ones, bound by the FP64 pipe, in one-warp
+    // blocks on D3Q729 and two-warp ones on D3Q4913 (whose stage buffers are twice the size)
+    const int width0 = tensor ? (prec != LB_F64 ? 128 : (c->kind == 3 ? 64 : 32)) : kTile;
     if (line) tiles = make_tiles(c->nx_inst, tensor ? 32 : width0);
     c->max_tiles = line ? (long long)make_tiles(c->nx_inst, 32).size() : 0;
     c->sched.tile_width = line ? width0 : kTile;
@@ -317,6 +322,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&c->d_inst, sizeof(InstanceInfo) * grid->batch);
     if (e == cudaSuccess && line) e = cudaMalloc(&c->d_tiles, sizeof(int2) * c->max_tiles);
+    if (e == cudaSuccess && line && tensor) e = cudaMalloc(&c->d_btiles, sizeof(int2) * c->max_tiles);
     if (e == cudaSuccess && tensor) e = cudaMalloc(&c->d_plane, sizeof(int) * c->q);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghosts, c->elem * c->q * 2 * grid->batch);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ghostsd, sizeof(double) * c->q * 2 * grid->batch);
@@ -343,6 +349,14 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     }
     if (!tiles.empty())
         e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, v.stream);
+    // block tiles of the default width (a one-cell-per-block schedule leaves them unused until a
+    // warp-staged width is set)
+    const std::vector<int2> btiles = line && tensor ? make_tiles(c->nx_inst, width0) : std::vector<int2>();
+    if (e == cudaSuccess && !btiles.empty())
+        e = cudaMemcpyAsync(c->d_btiles, btiles.data(), sizeof(int2) * btiles.size(), cudaMemcpyHostToDevice,
+                            v.stream);
+    v.nbtiles = (int)btiles.size();
+    c->btile_width = width0;
     if (e == cudaSuccess && tensor)
         e = cudaMemcpyAsync(c->d_plane, c->perm.data(), sizeof(int) * c->q, cudaMemcpyHostToDevice, v.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_health, 0, 16, v.stream);
@@ -359,6 +373,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     }
     v.inst = c->d_inst;
     v.tiles = c->d_tiles;
+    v.btiles = c->d_btiles;
     v.plane_idx = c->d_plane;
     v.ghosts = c->d_ghosts;
     v.ghostsd = c->d_ghostsd;
@@ -516,14 +531,13 @@ lb_status check_pair(const lb_ctx *c, const void *fa, const void *fb, int nsteps
 // grid of the persistent launch: blocks_per_sm (0 = as many as fit) on every SM, at most one
 // block per tile
 long long persistent_grid(const lb_ctx *c) {
-    // blocks with work: one per tile, or per tile_width / 32 tiles on tensor-product sets
-    // (whose one-cell-per-block schedule, tile width 1, has no persistent form)
-    const long long wpb = c->kind >= 2 ? c->view.tile_width / 32 : 1;
-    if (wpb < 1) return 0;
+    // blocks with work: one per tile (block tiles on tensor-product sets, whose
+    // one-cell-per-block schedule, tile width 1, has no persistent form)
+    if (c->kind >= 2 && c->view.tile_width < 32) return 0;
     const int occ = c->ks->occupancy(c->view);
     if (occ < 1) return 0;
     const int bps = c->sched.blocks_per_sm > 0 ? std::min(c->sched.blocks_per_sm, occ) : occ;
-    const long long needed = (c->view.ntiles + wpb - 1) / wpb;
+    const long long needed = c->kind >= 2 ? c->view.nbtiles : c->view.ntiles;
     return std::max(1LL, std::min((long long)bps * c->num_sms, needed));
 }
 
@@ -560,15 +574,26 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
     if (s->blocks_per_sm < 0 || (s->persistent != 0 && s->persistent != 1)) return LB_ERR_INVALID;
     if (s->tensor_cores != 0 && s->tensor_cores != 1) return LB_ERR_INVALID;
     // tensor-core x-rows: the warp-staged kernels of float tensor-product lines with fixed ends
-    if (s->tensor_cores && (c->kind < 2 || c->prec != LB_F32 || !c->view.line || !c->view.fixedx || cell_blocks))
+    if (s->tensor_cores && (c->kind < 2 || c->prec != LB_F32 || !c->view.line || !c->view.fixedx || s->tile_width != 32))
         return LB_ERR_UNSUPPORTED;
     if (!c->view.line) {  // the box kernel has one fixed launch shape
         if (s->persistent || s->tile_width != kTile) return LB_ERR_UNSUPPORTED;
         c->sched = *s;
         return LB_OK;
     }
-    if (s->tile_width != c->view.tile_width && c->kind >= 2) {
-        c->view.tile_width = s->tile_width;  // block size only: the tiles stay 32 cells wide
+    if (c->kind >= 2) {
+        // the 32-cell tiles stay; the step kernels' block tiles follow the width
+        if (!cell_blocks && s->tile_width != c->btile_width) {
+            const std::vector<int2> bt = make_tiles(c->nx_inst, s->tile_width);
+            if ((long long)bt.size() > c->max_tiles) return LB_ERR_INVALID;
+            cudaError_t e = cudaMemcpyAsync(c->d_btiles, bt.data(), sizeof(int2) * bt.size(), cudaMemcpyHostToDevice,
+                                            c->view.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->view.stream);
+            if (e != cudaSuccess) return LB_ERR_CUDA;
+            c->view.nbtiles = (int)bt.size();
+            c->btile_width = s->tile_width;
+        }
+        c->view.tile_width = s->tile_width;
     } else if (s->tile_width != c->view.tile_width) {
         const std::vector<int2> tiles = make_tiles(c->nx_inst, s->tile_width);
         if ((long long)tiles.size() > c->max_tiles) return LB_ERR_INVALID;
@@ -605,7 +630,7 @@ extern "C" lb_status lb_autotune(lb_ctx *c, void *fa, void *fb, int trial_steps,
     for (int tc = 0; tc < ntc; ++tc)
         for (int wi = 0; wi < nwidths; ++wi) {
             const int width = c->view.line ? widths[wi] : kTile;
-            if (tc && width == 1) continue;
+            if (tc && width != 32) continue;  // the tensor-core x-rows run one warp per block
             cand.push_back(lb_schedule{width, 0, 0, tc, 0.0});  // one launch per step
             if (!c->view.line || width == 1) continue;
             const lb_schedule probe{width, 0, 1, tc, 0.0};

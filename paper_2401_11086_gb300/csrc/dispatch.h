@@ -45,6 +45,9 @@ struct CtxView {
     int plane_identity;  // 1: library population i is caller plane i (tensor-map staging applies)
     int tensor_cores;    // 1: float tensor-product lines with fixed ends sum their x-rows on the
                          // tensor cores (lb_schedule::tensor_cores)
+    // tensor-product lines: the step kernels' block tiles (instance, first x) of tile_width cells
+    const int2 *btiles;
+    int nbtiles;
 };
 
 using StepFn = cudaError_t (*)(const CtxView &, const void *fin, void *fout);
@@ -322,24 +325,26 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
     a.cd = v.c;
     a.step = v.step;
     a.tma = 0;
+    a.identity = v.plane_identity;
     return a;
 }
 
-// Tensor map of a state for the warp-staged kernels: [Q planes][stride elements], box of
-// kSeg x d (one x-row group). False when the staging cannot use it (caller order differs from
-// the library order, a plane stride or base address not on 16 bytes, coordinates beyond int32)
-// or the driver refuses it; the kernels then copy plane by plane.
-template <class L1, class T>
+// Tensor map of a state for the block-staged kernels: [Q planes][stride elements], box of
+// kSeg x d (one x-row group of a W-warp block tile). False when the staging cannot use it
+// (caller order differs from the library order, a plane stride or base address not on 16 bytes,
+// coordinates beyond int32) or the driver refuses it; the kernels then copy plane by plane.
+template <class L1, class T, int W>
 bool tp_encode_map(const CtxView &v, const void *state, CUtensorMap *m) {
     constexpr int Q = L1::Q1 * L1::Q1 * L1::Q1;
+    constexpr int kSeg = TPBlockStage<L1, T, W>::kSeg;
     const TensorMapEncodeFn enc = tensor_map_encoder();
     if (!enc || !v.plane_identity || !state) return false;
     if ((reinterpret_cast<unsigned long long>(state) & 15ull) != 0ull || (v.stride * (long long)sizeof(T)) % 16 != 0 ||
-        v.stride + 2 * TPWarpStage<L1, T>::kSeg >= (1ll << 31))
+        v.stride + 2 * kSeg >= (1ll << 31))
         return false;
     const cuuint64_t dims[2] = {cuuint64_t(v.stride), cuuint64_t(Q)};
     const cuuint64_t strides[1] = {cuuint64_t(v.stride) * sizeof(T)};
-    const cuuint32_t box[2] = {cuuint32_t(TPWarpStage<L1, T>::kSeg), cuuint32_t(L1::Q1)};
+    const cuuint32_t box[2] = {cuuint32_t(kSeg), cuuint32_t(L1::Q1)};
     const cuuint32_t estr[2] = {1u, 1u};
     return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
                const_cast<void *>(state), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -347,11 +352,11 @@ bool tp_encode_map(const CtxView &v, const void *state, CUtensorMap *m) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The warp-staged kernels may take more than the default 48 KB of dynamic shared memory:
-// raise the limit of each instantiation to what a 128-thread block needs, once per device
-// (the attribute belongs to the device the call is made on).
-template <auto Kernel, class L1, class T>
-cudaError_t tp_smem_limit() {
+// The block-staged kernels may take more than the default 48 KB of dynamic shared memory:
+// raise the limit of each instantiation to what its block needs, once per device (the
+// attribute belongs to the device the call is made on).
+template <auto Kernel>
+cudaError_t tp_smem_limit(size_t bytes) {
     constexpr int kDevices = 64;
     static std::atomic<int> state[kDevices];  // 0 not set, 1 set, 2 failed
     int dev = 0;
@@ -360,16 +365,38 @@ cudaError_t tp_smem_limit() {
     if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
     const int s = state[dev].load(std::memory_order_acquire);
     if (s == 1) return cudaSuccess;
-    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TPWarpStage<L1, T>::bytes(128)));
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     state[dev].store(e == cudaSuccess ? 1 : 2, std::memory_order_release);
     return e;
 }
 
-// Tensor-product contexts keep 32-cell tiles; the schedule's tile width is the block size
-// (tile_width / 32 warps, one tile each).
-inline int tp_blocks(const CtxView &v) {
-    const int wpb = v.tile_width / 32;
-    return (v.ntiles + wpb - 1) / wpb;
+// Tensor-product lines step in block tiles of tile_width cells (tile_width / 32 warps, one
+// 32-cell row of the tile each); the other tensor-product kernels keep 32-cell tiles.
+template <class L1, int N, class T, int W, bool FixedX, bool TC>
+cudaError_t tp_launch_block(const CtxView &v, TPArgs<T> a, const void *fin) {
+    constexpr size_t smem = TPBlockStage<L1, T, W>::kBytes;
+    TPMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    a.tma = tp_encode_map<L1, T, W>(v, fin, &maps.src) ? 1 : 0;
+    a.tiles = v.btiles;
+    const cudaError_t e = tp_smem_limit<tp_step_line_block<L1, N, T, W, FixedX, TC>>(smem);
+    if (e != cudaSuccess) return e;
+    tp_step_line_block<L1, N, T, W, FixedX, TC><<<v.nbtiles, 32 * W, smem, v.stream>>>(a, v.nbtiles, maps);
+    return cudaGetLastError();
+}
+
+template <class L1, int N, class T, bool FixedX, bool TC>
+cudaError_t tp_launch_block_w(const CtxView &v, const TPArgs<T> &a, const void *fin) {
+    switch (v.tile_width) {
+        case 32: return tp_launch_block<L1, N, T, 1, FixedX, TC>(v, a, fin);
+        case 64:
+            if constexpr (!TC) return tp_launch_block<L1, N, T, 2, FixedX, false>(v, a, fin);
+            return cudaErrorInvalidConfiguration;
+        case 128:
+            if constexpr (!TC) return tp_launch_block<L1, N, T, 4, FixedX, false>(v, a, fin);
+            return cudaErrorInvalidConfiguration;
+        default: return cudaErrorInvalidConfiguration;
+    }
 }
 
 template <class L1, int N, class T>
@@ -386,28 +413,10 @@ cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
             return cudaErrorInvalidConfiguration;
         }
     }
-    const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
-    TPMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
-    a.tma = tp_encode_map<L1, T>(v, fin, &maps.src) ? 1 : 0;
-    if constexpr (std::is_same<T, float>::value) {
-        if (v.fixedx && v.tensor_cores) {
-            const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true, true>, L1, T>();
-            if (e != cudaSuccess) return e;
-            tp_step_line_warp<L1, N, T, true, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
-            return cudaGetLastError();
-        }
-    }
-    if (v.fixedx) {
-        const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, true>, L1, T>();
-        if (e != cudaSuccess) return e;
-        tp_step_line_warp<L1, N, T, true><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
-    } else {
-        const cudaError_t e = tp_smem_limit<tp_step_line_warp<L1, N, T, false>, L1, T>();
-        if (e != cudaSuccess) return e;
-        tp_step_line_warp<L1, N, T, false><<<tp_blocks(v), v.tile_width, smem, v.stream>>>(a, v.ntiles, maps);
-    }
-    return cudaGetLastError();
+    if constexpr (std::is_same<T, float>::value)
+        if (v.fixedx && v.tensor_cores) return tp_launch_block_w<L1, N, T, true, true>(v, a, fin);
+    if (v.fixedx) return tp_launch_block_w<L1, N, T, true, false>(v, a, fin);
+    return tp_launch_block_w<L1, N, T, false, false>(v, a, fin);
 }
 
 template <class L1, int N, class T>
@@ -432,67 +441,68 @@ cudaError_t tp_launch_ghost(const CtxView &v, const double *states, int ninst, v
     return cudaGetLastError();
 }
 
-template <class L1, int N, class T>
-cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, int grid) {
-    TPArgs<T> a = make_tp_args<T>(v, fa, fb);
+// The persistent launch of the block-staged kernel (cooperative; grid given) and its number
+// of resident blocks per SM.
+template <class L1, int N, class T, int W, bool FixedX, bool TC>
+cudaError_t tp_persist_block(const CtxView &v, TPArgs<T> a, void *fa, void *fb, int nsteps, int grid, int *occ) {
+    constexpr size_t smem = TPBlockStage<L1, T, W>::kBytes;
+    constexpr auto kernel = tp_step_line_persistent_block<L1, N, T, W, FixedX, TC>;
+    cudaError_t e = tp_smem_limit<kernel>(smem);
+    if (e != cudaSuccess) return e;
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, 32 * W, smem);
     TPMaps maps;
     std::memset(&maps, 0, sizeof(maps));
-    a.tma = (tp_encode_map<L1, T>(v, fa, &maps.src) && tp_encode_map<L1, T>(v, fb, &maps.dst)) ? 1 : 0;
+    a.tma = (tp_encode_map<L1, T, W>(v, fa, &maps.src) && tp_encode_map<L1, T, W>(v, fb, &maps.dst)) ? 1 : 0;
+    a.tiles = v.btiles;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(v.tile_width);
-    cfg.dynamicSmemBytes = TPWarpStage<L1, T>::bytes(v.tile_width);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = v.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const int ntiles = v.ntiles;
+    const int ntiles = v.nbtiles;
     unsigned *bar = v.bar;
-    if constexpr (std::is_same<T, float>::value) {
-        if (v.fixedx && v.tensor_cores) {
-            const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true, true>, L1, T>();
-            if (e != cudaSuccess) return e;
-            return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true, true>, a, nsteps, ntiles, bar,
-                                      maps);
-        }
+    return cudaLaunchKernelEx(&cfg, kernel, a, nsteps, ntiles, bar, maps);
+}
+
+template <class L1, int N, class T, bool FixedX, bool TC>
+cudaError_t tp_persist_block_w(const CtxView &v, const TPArgs<T> &a, void *fa, void *fb, int nsteps, int grid,
+                               int *occ) {
+    switch (v.tile_width) {
+        case 32: return tp_persist_block<L1, N, T, 1, FixedX, TC>(v, a, fa, fb, nsteps, grid, occ);
+        case 64:
+            if constexpr (!TC) return tp_persist_block<L1, N, T, 2, FixedX, false>(v, a, fa, fb, nsteps, grid, occ);
+            return cudaErrorInvalidConfiguration;
+        case 128:
+            if constexpr (!TC) return tp_persist_block<L1, N, T, 4, FixedX, false>(v, a, fa, fb, nsteps, grid, occ);
+            return cudaErrorInvalidConfiguration;
+        default: return cudaErrorInvalidConfiguration;
     }
-    if (v.fixedx) {
-        const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
-        if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, true>, a, nsteps, ntiles, bar, maps);
-    }
-    const cudaError_t e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, false>, L1, T>();
-    if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, tp_step_line_persistent_warp<L1, N, T, false>, a, nsteps, ntiles, bar, maps);
+}
+
+// occ non-null: report the resident blocks per SM instead of launching
+template <class L1, int N, class T>
+cudaError_t tp_persist_dispatch(const CtxView &v, void *fa, void *fb, int nsteps, int grid, int *occ) {
+    const TPArgs<T> a = make_tp_args<T>(v, fa, fb);
+    if constexpr (std::is_same<T, float>::value)
+        if (v.fixedx && v.tensor_cores) return tp_persist_block_w<L1, N, T, true, true>(v, a, fa, fb, nsteps, grid, occ);
+    if (v.fixedx) return tp_persist_block_w<L1, N, T, true, false>(v, a, fa, fb, nsteps, grid, occ);
+    return tp_persist_block_w<L1, N, T, false, false>(v, a, fa, fb, nsteps, grid, occ);
+}
+
+template <class L1, int N, class T>
+cudaError_t tp_launch_persistent(const CtxView &v, void *fa, void *fb, int nsteps, int grid) {
+    return tp_persist_dispatch<L1, N, T>(v, fa, fb, nsteps, grid, nullptr);
 }
 
 template <class L1, int N, class T>
 int tp_persistent_occupancy(const CtxView &v) {
     int n = 0;
-    const size_t smem = TPWarpStage<L1, T>::bytes(v.tile_width);
-    cudaError_t e;
-    if constexpr (std::is_same<T, float>::value) {
-        if (v.fixedx && v.tensor_cores) {
-            e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true, true>, L1, T>();
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, true, true>,
-                                                                  v.tile_width, smem);
-            return e == cudaSuccess ? n : 0;
-        }
-    }
-    if (v.fixedx) {
-        e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, true>, L1, T>();
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, true>,
-                                                              v.tile_width, smem);
-    } else {
-        e = tp_smem_limit<tp_step_line_persistent_warp<L1, N, T, false>, L1, T>();
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tp_step_line_persistent_warp<L1, N, T, false>,
-                                                              v.tile_width, smem);
-    }
+    const cudaError_t e = tp_persist_dispatch<L1, N, T>(v, nullptr, nullptr, 1, 1, &n);
     return e == cudaSuccess ? n : 0;
 }
 

@@ -66,6 +66,7 @@ struct TPArgs {
     double cd;                         // lattice scale c
     unsigned step;
     int tma;                           // 1: the kernel's tensor maps describe fin and fout
+    int identity;                      // 1: library population i is caller plane i
 };
 
 // Tensor maps of the two states for the warp-staged kernels: a 2D view [plane][stride] of a
@@ -75,21 +76,23 @@ struct TPMaps {
     CUtensorMap dst;  // of TPArgs::fout
 };
 
-// Shared-memory tables of one block: caller planes, the 1D abscissae (integers, as T) and the
-// 1D weights (as T).
-template <class L1, class T>
+// Shared-memory tables of one block: caller planes (Planes; the block-staged step reads them
+// from global memory, and only when the caller's order is not the library's), the 1D abscissae
+// (integers, as T) and the 1D weights (as T).
+template <class L1, class T, bool Planes = true>
 struct TPTables {
     static constexpr int Q = L1::Q1 * L1::Q1 * L1::Q1;
     static constexpr int kPow = 6;  // powers e^0 .. e^5 (N <= 5)
-    int plane[Q];
+    int plane[Planes ? Q : 1];
     T e[L1::Q1];
     T w[L1::Q1];
     T pw[L1::Q1][kPow];  // e_a^k: the y and z passes read them instead of forming them per cell
 };
 
-template <class L1, class T, class U>
-SMRT_D void tp_load_tables(const TPArgs<T> &a, TPTables<L1, U> &s) {
-    for (int i = threadIdx.x; i < TPTables<L1, U>::Q; i += blockDim.x) s.plane[i] = a.plane_idx[i];
+template <class L1, class T, class U, bool Planes>
+SMRT_D void tp_load_tables(const TPArgs<T> &a, TPTables<L1, U, Planes> &s) {
+    if constexpr (Planes)
+        for (int i = threadIdx.x; i < TPTables<L1, U>::Q; i += blockDim.x) s.plane[i] = a.plane_idx[i];
     if (threadIdx.x < L1::Q1) {
         const U ea = U(e1<L1>(threadIdx.x));
         s.e[threadIdx.x] = ea;
@@ -642,30 +645,42 @@ struct TPCell {
     }
 };
 
-// ------------------------------------------------------------------ warp-staged line tile
-// Each warp owns a tile of 32 cells and its own copy pipeline, so no block-wide barrier is
-// ever taken inside a step. The step's d^3 pulls per cell reach shared memory by stage: stage
-// st covers z-plane c = st / (NP1 + 1) and, within it, either the rest x-row (e_b = 0, d
-// planes) or the pair of x-rows +e_b, -e_b (2 d planes). Each plane arrives as one contiguous
-// x-segment [x0 - k - E_max, x0 + 31 - k + E_max] (every pull of the tile, rounded out to 16
-// bytes), copied by the bulk-copy engine; kStages fills are in flight per warp, each counted
-// in bytes on its own mbarrier.
-template <class L1, class T>
-struct TPWarpStage {
-    static constexpr int kW = 32;                       // cells per warp tile
-    static constexpr int kStages = 3;                   // fills in flight per warp
+// One plain arrival on mbarrier b (a warp's release of a stage buffer).
+SMRT_D void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+// ------------------------------------------------------------------ block-staged line tile
+// A block of W warps owns a tile of 32 W consecutive cells of one line (warp w takes cells
+// 32 w .. 32 w + 31, one per lane) and one copy pipeline. The step's d^3 pulls per cell reach
+// shared memory by stage: stage st covers z-plane c = st / (NP1 + 1) and, within it, either the
+// rest x-row (e_b = 0, d planes) or the pair of x-rows +e_b, -e_b (2 d planes). Each plane
+// arrives as one contiguous x-segment [x0 - k - E_max, x0 + 32 W - 1 - k + E_max] (every pull of
+// the tile, rounded out to 16 bytes) that all the block's warps read, so a halo of 2 E_max is
+// loaded once per 32 W cells and each copied row is 32 W cells long. kStages fills are in
+// flight: each buffer has a "full" mbarrier (the copy's bytes) and an "empty" one (one arrival
+// per warp that is done with the buffer), which warp 0 waits on before refilling it. No
+// block-wide barrier is taken inside a tile; the warps drift up to kStages stages apart.
+// (Measured on 512 Table 3 shocks, D3Q729 float, 128-cell tiles: 0.248 ms per step; five
+// stages 0.271 ms; refills issued by whichever warp releases a buffer last, counted by shared
+// atomics, 0.259 ms; one warp per tile, 0.287 ms.)
+template <class L1, class T, int W>
+struct TPBlockStage {
+    static constexpr int kW = 32 * W;                   // cells per block tile
+    static constexpr int kStages = 3;                   // fills in flight per block
     static constexpr int kAlign = 16 / int(sizeof(T));  // elements per 16 bytes
     static constexpr int kEmax = L1::E(L1::NP1 - 1);    // largest |e| of the 1D rule
     static constexpr int kSeg = kW + ((2 * kEmax + kAlign - 1) + kAlign - 1) / kAlign * kAlign;
+    static_assert(kSeg <= 256, "a tensor-map box spans at most 256 elements");
     // a stage buffer holds two groups of d rows (the +e_b and -e_b x-rows), each group
     // starting 128-byte aligned so that one tensor-map box fills it
     static constexpr int kGrp = int((L1::Q1 * kSeg * sizeof(T) + 127) / 128 * 128 / sizeof(T));
     static constexpr int kStage = 2 * kGrp;             // elements per stage buffer
     static constexpr int kPerZ = L1::NP1 + 1;           // stages per z-plane
     static constexpr int kTotal = L1::Q1 * kPerZ;       // stages per step
-    static constexpr size_t kWarpBytes =                // mbarriers, then the stage buffers
-        128 + size_t(kStages) * kStage * sizeof(T);
-    SMRT_HD static size_t bytes(int threads) { return size_t(threads / 32) * kWarpBytes; }
+    static_assert(kTotal % kStages == 0, "each tile starts the buffers' cycle at buffer 0");
+    static_assert(kStages * 16 <= 128, "the full and empty mbarriers fit the 128-byte head");
+    static constexpr size_t kBytes = 128 + size_t(kStages) * kStage * sizeof(T);  // mbarriers, buffers
 };
 
 // ------------------------------------------------------------------ x-row sums on tensor cores
@@ -773,19 +788,22 @@ struct TPTensorRows {
     }
 };
 
-// One warp tile of the step. buf, bar: the warp's stage buffers and mbarriers; bit b of parity
-// is the parity of buffer b's next fill, bit b of pending says that fill is in flight. All 32
-// lanes call it (lanes past the line's end idle). Returns false, with LB_HEALTH_TIMEOUT in
-// the health word, when a fill did not land within the bounded wait.
+// One block tile of the step; every thread of the block calls it. buf, full, empty: the block's
+// stage buffers and their mbarriers; nt: tiles this block has stepped before (the buffers'
+// phases follow from it: each tile makes kTotal / kStages uses of every buffer). Returns false,
+// with LB_HEALTH_TIMEOUT in the health word, when a wait did not end within its bound (warp 0
+// then lets the fills it has in flight land before it leaves).
 // tm: tensor map of fin (one box per x-row group), or null to copy plane by plane.
-// TC (float only): the x-row sums of every stage on the tensor cores (TPTensorRows).
-template <class L1, int N, class T, bool FixedX, bool Coherent, bool TC = false>
-SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *__restrict__ fin,
-                         T *__restrict__ fout, int tile_index, T *buf, unsigned long long *bar, unsigned &parity,
-                         unsigned &pending, const CUtensorMap *tm) {
+// TC (float, one warp per block): the x-row sums of every stage on the tensor cores.
+template <class L1, int N, class T, int W, bool FixedX, bool Coherent, bool TC = false>
+SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, const T *__restrict__ fin,
+                          T *__restrict__ fout, int tile_index, T *buf, unsigned long long *full,
+                          unsigned long long *empty, unsigned nt, const CUtensorMap *tm) {
     using C = TPCell<L1, N, T>;
-    using S = TPWarpStage<L1, T>;
+    using S = TPBlockStage<L1, T, W>;
     static_assert(N + 1 <= TPTables<L1, T>::kPow, "the powers table holds e^0 .. e^5");
+    static_assert(!TC || (W == 1 && std::is_same<T, float>::value),
+                  "tensor-core x-rows: float states, one warp per block (its stage buffer is its scratch)");
     constexpr int Q1 = L1::Q1;
     constexpr int NP1 = L1::NP1;
     constexpr int P2 = Q1 * Q1;
@@ -793,10 +811,10 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
     constexpr int EM = S::kEmax;
     constexpr int SEG = S::kSeg;
     constexpr int NS = S::kStages;
-    const int lane = threadIdx.x & 31;
+    const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
     const int2 tile = a.tiles[tile_index];
     const InstanceInfo &in = a.inst[tile.x];
-    const int x0 = tile.y, x = x0 + lane, L = in.nx, kx = in.kx;
+    const int x0 = tile.y, x = x0 + 32 * warp + lane, L = in.nx, kx = in.kx;
     const bool active = x < L;
     const long long base = in.cell_off;
     const T *gl = a.ghosts + (long long)tile.x * 2 * Q;
@@ -807,13 +825,23 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
     const long long ce = (g_al + SEG < a.stride) ? g_al + SEG : a.stride;
     const unsigned nbytes = unsigned((ce - cs) * (long long)sizeof(T));
     const int dst_off = int(cs - g_al);
-    auto issue = [&](int st) {
+    const unsigned long long u0 = (unsigned long long)nt * (S::kTotal / NS);  // earlier uses of each buffer
+    // caller plane of library population i
+    auto plane = [&](int i) -> long long { return a.identity ? i : __ldg(a.plane_idx + i); };
+    // warp 0: bit b of pending says buffer b has a fill issued and not yet waited for, bit b of
+    // fpar is that fill's phase parity
+    unsigned pending = 0u, fpar = 0u;
+    // warp 0 only: refill the buffer of stage st once every warp has released its previous fill
+    auto issue = [&](int st) -> bool {
         const int sb = st % NS;
+        const unsigned long long u = u0 + (unsigned long long)(st / NS);  // this fill is use u of buffer sb
+        if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(empty + sb, unsigned((u - 1) & 1ull)))) return false;
         pending |= 1u << sb;
+        fpar = (fpar & ~(1u << sb)) | (unsigned(u & 1ull) << sb);
         const int cz = st / S::kPerZ, p = st % S::kPerZ;
         const int nplanes = p ? 2 * Q1 : Q1;
         const int k0 = p ? (2 * p - 1) * Q1 : 0;  // in-plane index of the stage's first population
-        unsigned long long *b = bar + sb;
+        unsigned long long *b = full + sb;
         T *sbuf = buf + size_t(sb) * S::kStage;
         if constexpr (Coherent) fence_async_global();
         fence_async_shared();
@@ -825,10 +853,19 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
             }
         } else {
             if (lane == 0) mbar_arrive_expect_tx(b, unsigned(nplanes) * nbytes);
+            __syncwarp();
             for (int k = lane; k < nplanes; k += 32)  // a pair stage of D1Q17 has 34 planes
                 bulk_copy_g2s(sbuf + (k / Q1) * S::kGrp + (k % Q1) * SEG + dst_off,
-                              fin + (long long)s.plane[cz * P2 + k0 + k] * a.stride + cs, nbytes, b);
+                              fin + plane(cz * P2 + k0 + k) * a.stride + cs, nbytes, b);
         }
+        return true;
+    };
+    auto fail = [&]() -> bool {
+        if (lane == 0) atomicOr(a.health, 2u);
+        // warp 0: let the fills still in flight land before the block can leave (each wait bounded)
+        for (int q = 0; q < NS; ++q)
+            if ((pending >> q) & 1u) mbar_wait(full + q, (fpar >> q) & 1u);
+        return false;
     };
     // the lane's pull by x-velocity a of a staged row sits at row + a SEG + tb - e_a; each
     // (plane, slot) is read by this lane only, so the lane may overwrite its own slots
@@ -842,13 +879,14 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
             const int t = x - e1<L1>(av) - kx;
             if (t < 0 || t >= L) beyond |= 1u << av;
         });
-    static_assert(!TC || std::is_same<T, float>::value, "tensor-core x-rows are TF32 (float states)");
+    if (warp == 0)
+        for (int st = 0; st < NS; ++st)
+            if (!issue(st)) return fail();
     TPTensorRows<L1, N> tc;
     if constexpr (TC) {
         static_assert(2 * 32 * TPTensorRows<L1, N>::kPitch <= S::kStage, "scratch fits a stage buffer");
         tc.init(lane, SEG);
     }
-    for (int st = 0; st < NS; ++st) issue(st);
     T R[C::M];
     static_for<C::M>([&](auto G) { R[decltype(G)::value] = T(0); });
     T h[N + 1][N + 1];
@@ -858,39 +896,30 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
 #pragma unroll 1
     for (int st = 0; st < S::kTotal; ++st) {
         const int sb = st % NS;
-        const bool landed = __all_sync(0xffffffffu, mbar_wait(bar + sb, (parity >> sb) & 1u));
-        if (!landed) {
-            if (lane == 0) atomicOr(a.health, 2u);
-            // let fills still in flight land before the warp moves on (each wait bounded)
-            for (int q = 0; q < NS; ++q)
-                if ((pending >> q) & 1u) mbar_wait(bar + q, (parity >> q) & 1u);
-            return false;
-        }
-        parity ^= 1u << sb;
+        const unsigned long long u = u0 + (unsigned long long)(st / NS);
+        if (!__all_sync(0xffffffffu, mbar_wait(full + sb, unsigned(u & 1ull)))) return fail();
         pending &= ~(1u << sb);
         const int cz = st / S::kPerZ, p = st % S::kPerZ;
         T *bs = buf + size_t(sb) * S::kStage;
-        if (active) {
-            if (beyond) {
-                const int nrows = p ? 2 : 1;
-                const int k0 = p ? (2 * p - 1) * Q1 : 0;
-                static_for<Q1>([&](auto A) {
-                    constexpr int av = decltype(A)::value;
-                    if ((beyond >> av) & 1u) {
-                        const int t = x - e1<L1>(av) - kx;
-                        for (int r = 0; r < nrows; ++r) {
-                            const int i = cz * P2 + k0 + r * Q1 + av;
-                            T v;
-                            if constexpr (FixedX)
-                                v = t < 0 ? gl[i] : gr[i];
-                            else
-                                v = load_pop<Coherent>(fin + (long long)s.plane[i] * a.stride + base + wrap(t, L));
-                            bs[r * S::kGrp + av * SEG + tb - e1<L1>(av)] = v;
-                        }
+        if (active && beyond) {
+            const int nrows = p ? 2 : 1;
+            const int k0 = p ? (2 * p - 1) * Q1 : 0;
+            static_for<Q1>([&](auto A) {
+                constexpr int av = decltype(A)::value;
+                if ((beyond >> av) & 1u) {
+                    const int t = x - e1<L1>(av) - kx;
+                    for (int r = 0; r < nrows; ++r) {
+                        const int i = cz * P2 + k0 + r * Q1 + av;
+                        T v;
+                        if constexpr (FixedX)
+                            v = t < 0 ? gl[i] : gr[i];
+                        else
+                            v = load_pop<Coherent>(fin + plane(i) * a.stride + base + wrap(t, L));
+                        bs[r * S::kGrp + av * SEG + tb - e1<L1>(av)] = v;
                     }
-                });
-                fence_async_shared();  // own slots rewritten: before the buffer's next fill
-            }
+                }
+            });
+            fence_async_shared();  // own slots rewritten: before the buffer's next fill
         }
         if constexpr (TC) {
             __syncwarp();  // the rewritten slots are operands of other lanes
@@ -928,14 +957,15 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
             }
             if (p == NP1) C::zfold_pw(h, s.pw[cz], R);
         }
-        __syncwarp();  // every lane is done with buffer sb
-        if (st + NS < S::kTotal) issue(st + NS);
+        __syncwarp();  // every lane of this warp is done with buffer sb
+        if (lane == 0) mbar_arrive(empty + sb);
+        if (warp == 0 && st + NS < S::kTotal && !issue(st + NS)) return fail();
     }
     if (active) {
         const bool ok = C::collide_moments(R, T(a.cd), tau_a<T>(in), tau_b<T>(in), in.model, T(in.es_b));
         if (!ok) atomicOr(a.health, 1u);
         T *dst = fout + base + x;
-        auto put = [&](int i, T v) { dst[(long long)s.plane[i] * a.stride] = v; };
+        auto put = [&](int i, T v) { dst[plane(i) * a.stride] = v; };
 #pragma unroll 1
         for (int cz = 0; cz < Q1; ++cz) {
             T Pc[N + 1][N + 1];
@@ -959,64 +989,71 @@ SMRT_D bool tp_warp_tile(const TPArgs<T> &a, const TPTables<L1, T> &s, const T *
     return true;
 }
 
-template <class L1, class T>
-SMRT_D void tp_warp_setup(unsigned char *dyn, unsigned long long *&bar, T *&buf) {
-    using S = TPWarpStage<L1, T>;
-    unsigned char *mine = dyn + size_t(threadIdx.x >> 5) * S::kWarpBytes;
-    bar = reinterpret_cast<unsigned long long *>(mine);
-    buf = reinterpret_cast<T *>(mine + 128);
-    if ((threadIdx.x & 31) == 0) {
-        for (int q = 0; q < S::kStages; ++q) mbar_init(bar + q, 1);
+// The block's mbarriers (full[kStages], then empty[kStages]) and stage buffers in dynamic
+// shared memory; thread 0 initialises the barriers (published by the block barrier that
+// follows in the kernel).
+template <class L1, class T, int W>
+SMRT_D void tp_block_setup(unsigned char *dyn, unsigned long long *&full, unsigned long long *&empty, T *&buf) {
+    using S = TPBlockStage<L1, T, W>;
+    full = reinterpret_cast<unsigned long long *>(dyn);
+    empty = full + S::kStages;
+    buf = reinterpret_cast<T *>(dyn + 128);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S::kStages; ++q) {
+            mbar_init(full + q, 1);
+            mbar_init(empty + q, W);
+        }
         fence_mbar_init();
     }
 }
 
-// One step: warp w of block b takes the 32-cell tile b * (blockDim / 32) + w.
+// One step: block b (W warps) takes the block tile b.
 // maps: tensor maps of the two states, used when a.tma is set (and the dynamic shared memory
 // is 128-byte aligned, as the boxes need).
-template <class L1, int N, class T, bool FixedX, bool TC = false>
-__global__ void __launch_bounds__(128) tp_step_line_warp(TPArgs<T> a, int ntiles, const __grid_constant__ TPMaps maps) {
-    __shared__ TPTables<L1, T> s;
+template <class L1, int N, class T, int W, bool FixedX, bool TC = false>
+__global__ void __launch_bounds__(128) tp_step_line_block(TPArgs<T> a, int ntiles, const __grid_constant__ TPMaps maps) {
+    __shared__ TPTables<L1, T, false> s;
     extern __shared__ __align__(128) unsigned char dyn[];
-    unsigned long long *bar;
+    unsigned long long *full, *empty;
     T *buf;
-    tp_warp_setup<L1>(dyn, bar, buf);
+    tp_block_setup<L1, T, W>(dyn, full, empty, buf);
     tp_load_tables<L1>(a, s);  // ends with __syncthreads
-    const int t = blockIdx.x * int(blockDim.x >> 5) + int(threadIdx.x >> 5);
+    const int t = blockIdx.x;
     if (t >= ntiles) return;
-    unsigned parity = 0u, pending = 0u;
     const CUtensorMap *tm = (a.tma && (smem_addr(dyn) & 127u) == 0u) ? &maps.src : nullptr;
-    tp_warp_tile<L1, N, T, FixedX, false, TC>(a, s, a.fin, a.fout, t, buf, bar, parity, pending, tm);
+    tp_block_tile<L1, N, T, W, FixedX, false, TC>(a, s, a.fin, a.fout, t, buf, full, empty, 0u, tm);
 }
 
 // All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh); the
-// warps stride over the 32-cell tiles.
-template <class L1, int N, class T, bool FixedX, bool TC = false>
-__global__ void __launch_bounds__(128) tp_step_line_persistent_warp(TPArgs<T> a, int nsteps, int ntiles,
-                                                                    unsigned *barg, const __grid_constant__ TPMaps maps) {
-    __shared__ TPTables<L1, T> s;
+// blocks stride over the block tiles.
+template <class L1, int N, class T, int W, bool FixedX, bool TC = false>
+__global__ void __launch_bounds__(128) tp_step_line_persistent_block(TPArgs<T> a, int nsteps, int ntiles,
+                                                                     unsigned *barg, const __grid_constant__ TPMaps maps) {
+    __shared__ TPTables<L1, T, false> s;
     __shared__ int failed;
     extern __shared__ __align__(128) unsigned char dyn[];
-    unsigned long long *bar;
+    unsigned long long *full, *empty;
     T *buf;
-    tp_warp_setup<L1>(dyn, bar, buf);
+    tp_block_setup<L1, T, W>(dyn, full, empty, buf);
     if (threadIdx.x == 0) failed = 0;
     tp_load_tables<L1>(a, s);
-    const int wpb = int(blockDim.x >> 5);
-    unsigned parity = 0u, pending = 0u;
     unsigned gen = 0;
     if (threadIdx.x == 0) gen = atomicAdd(&barg[1], 0u);
     const unsigned step0 = __ldcg(&barg[2]);
     const T *src = a.fin;
     T *dst = a.fout;
     const bool use_tma = a.tma && (smem_addr(dyn) & 127u) == 0u;
+    unsigned nt = 0;  // tiles this block has stepped
     for (int st = 0; st < nsteps; ++st) {
         const CUtensorMap *tm = use_tma ? (src == a.fin ? &maps.src : &maps.dst) : nullptr;
-        for (int t = blockIdx.x * wpb + int(threadIdx.x >> 5); t < ntiles; t += gridDim.x * wpb)
-            if (!tp_warp_tile<L1, N, T, FixedX, true, TC>(a, s, src, dst, t, buf, bar, parity, pending, tm)) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (*static_cast<volatile int *>(&failed)) break;  // another warp gave up
+            if (!tp_block_tile<L1, N, T, W, FixedX, true, TC>(a, s, src, dst, t, buf, full, empty, nt, tm)) {
                 failed = 1;
                 break;
             }
+            ++nt;
+        }
         __syncthreads();
         if (failed) return;
         if (st + 1 < nsteps) {

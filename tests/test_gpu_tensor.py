@@ -453,7 +453,7 @@ def test_mixed_mach_batch_graph_replay_against_golden(lat, prec, tol_rho, tol_q)
 
 
 # ------------------------------------------------------------------ x-row sums on tensor cores
-@pytest.mark.parametrize("sched", [(64, 0, 0), (32, 0, 0), (128, 2, 1)])
+@pytest.mark.parametrize("sched", [(32, 0, 0), (32, 2, 1)])
 def test_tensor_core_xrows_table3_f32(lat, sched):
     """FP32 with the x-row sums of the projection on the tensor cores (TF32 operands split in
     two, three products): the three Table 3 rows in one batch from the step start, 8 steps,
@@ -494,7 +494,7 @@ def test_tensor_core_xrows_ma7_d3q4913_f32(lat17):
         for _ in range(nsteps):
             h = OS.step(h, case.model, case.geom)
         wants.append(h.reshape(olat.q, -1))
-    for mode, sched in [("step", (64, 0, 0)), ("step", (64, 1, 1)), ("graph", (32, 2, 1))]:
+    for mode, sched in [("step", (32, 0, 0)), ("step", (32, 1, 1)), ("graph", (32, 2, 1))]:
         P.lb_set_schedule(ctx, *sched, tensor_cores=1)
         fa, fb = f0.clone(), ctx.new_state()
         out = P.lb_step_graph(ctx, fa, fb, nsteps) if mode == "graph" else P.lb_step(ctx, fa, fb, nsteps)
@@ -505,7 +505,7 @@ def test_tensor_core_xrows_ma7_d3q4913_f32(lat17):
 
 
 def test_tensor_core_xrows_refused_where_not_built(lat):
-    """tensor_cores applies to float tensor-product lines with fixed ends only."""
+    """tensor_cores applies to float tensor-product lines with fixed ends, one warp per block."""
     olat, d, idx = lat
     ctx64, _, _ = shocks.setup_batch(d, 5, [3.0], [40], precision="f64", width=0.0, theta1=[0.333])
     with pytest.raises(P.SmrtError):
@@ -514,8 +514,10 @@ def test_tensor_core_xrows_refused_where_not_built(lat):
     with pytest.raises(P.SmrtError):
         P.lb_set_schedule(ctx32, 1, 0, 0, tensor_cores=1)   # one block per cell
     with pytest.raises(P.SmrtError):
-        P.lb_set_schedule(ctx32, 64, 0, 0, tensor_cores=2)
-    P.lb_set_schedule(ctx32, 64, 0, 0, tensor_cores=1)
+        P.lb_set_schedule(ctx32, 32, 0, 0, tensor_cores=2)
+    with pytest.raises(P.SmrtError):
+        P.lb_set_schedule(ctx32, 64, 0, 0, tensor_cores=1)   # block tiles of two warps
+    P.lb_set_schedule(ctx32, 32, 0, 0, tensor_cores=1)
     per = P.lb_init_lattice(_desc(d, (2, 0, 0)), 40, N=5, precision="f32")
     with pytest.raises(P.SmrtError):
-        P.lb_set_schedule(per, 64, 0, 0, tensor_cores=1)  # periodic line
+        P.lb_set_schedule(per, 32, 0, 0, tensor_cores=1)  # periodic line
