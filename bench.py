@@ -475,9 +475,9 @@ def run_table3(args, world: int, rank: int, local: int) -> None:
     if args.es_b is not None:          # the ES-BGK model (Sec. 3) instead of SMRT
         P.lb_set_collision_model(ctx, -1, P.LB_MODEL_ES_BGK, args.es_b)
     if args.tensor_cores:              # the projection's x-row sums on the tensor cores
-        s0 = P.lb_get_schedule(ctx)
-        P.lb_set_schedule(ctx, s0["tile_width"] if s0["tile_width"] > 1 else 64, s0["blocks_per_sm"],
-                          s0["persistent"], tensor_cores=1)
+        P.lb_set_schedule(ctx, 32, 0, 0, tensor_cores=1)   # (one warp per block)
+    elif args.tile_width:
+        P.lb_set_schedule(ctx, args.tile_width, 0, 0)
     sched = P.lb_get_schedule(ctx)   # the library's choice for this size
     fa, fb = f0, ctx.new_state()
     cur = P.lb_step(ctx, fa, fb, args.warmup)
@@ -738,6 +738,8 @@ def main():
                     help="table3 workload: the D3Q729 rows (Ma 1.5/3/5) or the D3Q4913 row (Ma 7)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="table3 workload, f32: the projection's x-row sums on the tensor cores")
+    ap.add_argument("--tile-width", type=int, default=0,
+                    help="table3 workload: block tile width (32, 64, 128; 0: the library's default)")
     ap.add_argument("--length", type=int, default=0,
                     help="table3 workload: cells per shock (0: 100..400 by seed)")
     args = ap.parse_args()
