@@ -336,7 +336,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     }
     // D3Q729 problems of at most 48 (double) or 32 (float) cells per SM take one block per cell
-    // (measured crossovers with the warp-staged kernel)
+    // (measured crossovers with the tiled kernel)
     if (e == cudaSuccess && c->kind == 2 && (long long)ncells <= (prec == LB_F64 ? 48LL : 32LL) * c->num_sms) {
         c->sched.tile_width = 1;
         v.tile_width = 1;
@@ -350,7 +350,7 @@ extern "C" lb_status lb_init_lattice(lb_ctx **out, const lb_lattice_desc *lat, c
     if (!tiles.empty())
         e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, v.stream);
     // block tiles of the default width (a one-cell-per-block schedule leaves them unused until a
-    // warp-staged width is set)
+    // tiled width is set)
     const std::vector<int2> btiles = line && tensor ? make_tiles(c->nx_inst, width0) : std::vector<int2>();
     if (e == cudaSuccess && !btiles.empty())
         e = cudaMemcpyAsync(c->d_btiles, btiles.data(), sizeof(int2) * btiles.size(), cudaMemcpyHostToDevice,
@@ -573,7 +573,7 @@ extern "C" lb_status lb_set_schedule(lb_ctx *c, const lb_schedule *s) {
     if (cell_blocks && (c->kind != 2 || s->persistent)) return LB_ERR_UNSUPPORTED;
     if (s->blocks_per_sm < 0 || (s->persistent != 0 && s->persistent != 1)) return LB_ERR_INVALID;
     if (s->tensor_cores != 0 && s->tensor_cores != 1) return LB_ERR_INVALID;
-    // tensor-core x-rows: the warp-staged kernels of float tensor-product lines with fixed ends
+    // tensor-core x-rows: the block-staged kernels of float tensor-product lines with fixed ends
     if (s->tensor_cores && (c->kind < 2 || c->prec != LB_F32 || !c->view.line || !c->view.fixedx || s->tile_width != 32))
         return LB_ERR_UNSUPPORTED;
     if (!c->view.line) {  // the box kernel has one fixed launch shape

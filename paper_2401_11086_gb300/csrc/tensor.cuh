@@ -69,7 +69,7 @@ struct TPArgs {
     int identity;                      // 1: library population i is caller plane i
 };
 
-// Tensor maps of the two states for the warp-staged kernels: a 2D view [plane][stride] of a
+// Tensor maps of the two states for the block-staged kernels: a 2D view [plane][stride] of a
 // state (library order = caller order), box of kSeg elements x d planes (one x-row group).
 struct TPMaps {
     CUtensorMap src;  // of TPArgs::fin

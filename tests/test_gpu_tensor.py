@@ -192,8 +192,8 @@ def test_schedules_and_graph_agree(lat):
 @pytest.mark.parametrize("width", [1, 64])
 def test_caller_velocity_order_is_free(lat, width):
     """A context built on the oracle's own velocity order (any order is allowed) gives the
-    same populations as one in library order, under the one-cell kernel and the warp-staged
-    one. In library order the warp-staged kernel stages whole x-row groups with tensor-map
+    same populations as one in library order, under the one-cell kernel and the block-staged
+    one. In library order the block-staged kernel stages whole x-row groups with tensor-map
     boxes, in another order plane by plane: the data moved is the same, so the two agree
     bit for bit."""
     olat, d, idx = lat
