@@ -325,7 +325,6 @@ TPArgs<T> make_tp_args(const CtxView &v, const void *fin, void *fout) {
     a.cd = v.c;
     a.step = v.step;
     a.tma = 0;
-    a.identity = v.plane_identity;
     return a;
 }
 
@@ -372,28 +371,28 @@ cudaError_t tp_smem_limit(size_t bytes) {
 
 // Tensor-product lines step in block tiles of tile_width cells (tile_width / 32 warps, one
 // 32-cell row of the tile each); the other tensor-product kernels keep 32-cell tiles.
-template <class L1, int N, class T, int W, bool FixedX, bool TC>
+template <class L1, int N, class T, int W, bool FixedX, bool TC, bool Ident>
 cudaError_t tp_launch_block(const CtxView &v, TPArgs<T> a, const void *fin) {
     constexpr size_t smem = TPBlockStage<L1, T, W>::kBytes;
     TPMaps maps;
     std::memset(&maps, 0, sizeof(maps));
     a.tma = tp_encode_map<L1, T, W>(v, fin, &maps.src) ? 1 : 0;
     a.tiles = v.btiles;
-    const cudaError_t e = tp_smem_limit<tp_step_line_block<L1, N, T, W, FixedX, TC>>(smem);
+    const cudaError_t e = tp_smem_limit<tp_step_line_block<L1, N, T, W, FixedX, TC, Ident>>(smem);
     if (e != cudaSuccess) return e;
-    tp_step_line_block<L1, N, T, W, FixedX, TC><<<v.nbtiles, 32 * W, smem, v.stream>>>(a, v.nbtiles, maps);
+    tp_step_line_block<L1, N, T, W, FixedX, TC, Ident><<<v.nbtiles, 32 * W, smem, v.stream>>>(a, v.nbtiles, maps);
     return cudaGetLastError();
 }
 
-template <class L1, int N, class T, bool FixedX, bool TC>
+template <class L1, int N, class T, bool FixedX, bool TC, bool Ident>
 cudaError_t tp_launch_block_w(const CtxView &v, const TPArgs<T> &a, const void *fin) {
     switch (v.tile_width) {
-        case 32: return tp_launch_block<L1, N, T, 1, FixedX, TC>(v, a, fin);
+        case 32: return tp_launch_block<L1, N, T, 1, FixedX, TC, Ident>(v, a, fin);
         case 64:
-            if constexpr (!TC) return tp_launch_block<L1, N, T, 2, FixedX, false>(v, a, fin);
+            if constexpr (!TC) return tp_launch_block<L1, N, T, 2, FixedX, false, Ident>(v, a, fin);
             return cudaErrorInvalidConfiguration;
         case 128:
-            if constexpr (!TC) return tp_launch_block<L1, N, T, 4, FixedX, false>(v, a, fin);
+            if constexpr (!TC) return tp_launch_block<L1, N, T, 4, FixedX, false, Ident>(v, a, fin);
             return cudaErrorInvalidConfiguration;
         default: return cudaErrorInvalidConfiguration;
     }
@@ -413,10 +412,15 @@ cudaError_t tp_launch_step(const CtxView &v, const void *fin, void *fout) {
             return cudaErrorInvalidConfiguration;
         }
     }
+    // the lines with fixed ends in the library's plane order (the shock runs) take a form that
+    // stores without the plane table
     if constexpr (std::is_same<T, float>::value)
-        if (v.fixedx && v.tensor_cores) return tp_launch_block_w<L1, N, T, true, true>(v, a, fin);
-    if (v.fixedx) return tp_launch_block_w<L1, N, T, true, false>(v, a, fin);
-    return tp_launch_block_w<L1, N, T, false, false>(v, a, fin);
+        if (v.fixedx && v.tensor_cores)
+            return v.plane_identity ? tp_launch_block_w<L1, N, T, true, true, true>(v, a, fin)
+                                    : tp_launch_block_w<L1, N, T, true, true, false>(v, a, fin);
+    if (v.fixedx && v.plane_identity) return tp_launch_block_w<L1, N, T, true, false, true>(v, a, fin);
+    if (v.fixedx) return tp_launch_block_w<L1, N, T, true, false, false>(v, a, fin);
+    return tp_launch_block_w<L1, N, T, false, false, false>(v, a, fin);
 }
 
 template <class L1, int N, class T>
@@ -443,10 +447,10 @@ cudaError_t tp_launch_ghost(const CtxView &v, const double *states, int ninst, v
 
 // The persistent launch of the block-staged kernel (cooperative; grid given) and its number
 // of resident blocks per SM.
-template <class L1, int N, class T, int W, bool FixedX, bool TC>
+template <class L1, int N, class T, int W, bool FixedX, bool TC, bool Ident>
 cudaError_t tp_persist_block(const CtxView &v, TPArgs<T> a, void *fa, void *fb, int nsteps, int grid, int *occ) {
     constexpr size_t smem = TPBlockStage<L1, T, W>::kBytes;
-    constexpr auto kernel = tp_step_line_persistent_block<L1, N, T, W, FixedX, TC>;
+    constexpr auto kernel = tp_step_line_persistent_block<L1, N, T, W, FixedX, TC, Ident>;
     cudaError_t e = tp_smem_limit<kernel>(smem);
     if (e != cudaSuccess) return e;
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, 32 * W, smem);
@@ -469,16 +473,18 @@ cudaError_t tp_persist_block(const CtxView &v, TPArgs<T> a, void *fa, void *fb, 
     return cudaLaunchKernelEx(&cfg, kernel, a, nsteps, ntiles, bar, maps);
 }
 
-template <class L1, int N, class T, bool FixedX, bool TC>
+template <class L1, int N, class T, bool FixedX, bool TC, bool Ident>
 cudaError_t tp_persist_block_w(const CtxView &v, const TPArgs<T> &a, void *fa, void *fb, int nsteps, int grid,
                                int *occ) {
     switch (v.tile_width) {
-        case 32: return tp_persist_block<L1, N, T, 1, FixedX, TC>(v, a, fa, fb, nsteps, grid, occ);
+        case 32: return tp_persist_block<L1, N, T, 1, FixedX, TC, Ident>(v, a, fa, fb, nsteps, grid, occ);
         case 64:
-            if constexpr (!TC) return tp_persist_block<L1, N, T, 2, FixedX, false>(v, a, fa, fb, nsteps, grid, occ);
+            if constexpr (!TC)
+                return tp_persist_block<L1, N, T, 2, FixedX, false, Ident>(v, a, fa, fb, nsteps, grid, occ);
             return cudaErrorInvalidConfiguration;
         case 128:
-            if constexpr (!TC) return tp_persist_block<L1, N, T, 4, FixedX, false>(v, a, fa, fb, nsteps, grid, occ);
+            if constexpr (!TC)
+                return tp_persist_block<L1, N, T, 4, FixedX, false, Ident>(v, a, fa, fb, nsteps, grid, occ);
             return cudaErrorInvalidConfiguration;
         default: return cudaErrorInvalidConfiguration;
     }
@@ -489,9 +495,13 @@ template <class L1, int N, class T>
 cudaError_t tp_persist_dispatch(const CtxView &v, void *fa, void *fb, int nsteps, int grid, int *occ) {
     const TPArgs<T> a = make_tp_args<T>(v, fa, fb);
     if constexpr (std::is_same<T, float>::value)
-        if (v.fixedx && v.tensor_cores) return tp_persist_block_w<L1, N, T, true, true>(v, a, fa, fb, nsteps, grid, occ);
-    if (v.fixedx) return tp_persist_block_w<L1, N, T, true, false>(v, a, fa, fb, nsteps, grid, occ);
-    return tp_persist_block_w<L1, N, T, false, false>(v, a, fa, fb, nsteps, grid, occ);
+        if (v.fixedx && v.tensor_cores)
+            return v.plane_identity ? tp_persist_block_w<L1, N, T, true, true, true>(v, a, fa, fb, nsteps, grid, occ)
+                                    : tp_persist_block_w<L1, N, T, true, true, false>(v, a, fa, fb, nsteps, grid, occ);
+    if (v.fixedx && v.plane_identity)
+        return tp_persist_block_w<L1, N, T, true, false, true>(v, a, fa, fb, nsteps, grid, occ);
+    if (v.fixedx) return tp_persist_block_w<L1, N, T, true, false, false>(v, a, fa, fb, nsteps, grid, occ);
+    return tp_persist_block_w<L1, N, T, false, false, false>(v, a, fa, fb, nsteps, grid, occ);
 }
 
 template <class L1, int N, class T>

@@ -66,7 +66,6 @@ struct TPArgs {
     double cd;                         // lattice scale c
     unsigned step;
     int tma;                           // 1: the kernel's tensor maps describe fin and fout
-    int identity;                      // 1: library population i is caller plane i
 };
 
 // Tensor maps of the two states for the block-staged kernels: a 2D view [plane][stride] of a
@@ -795,7 +794,8 @@ struct TPTensorRows {
 // then lets the fills it has in flight land before it leaves).
 // tm: tensor map of fin (one box per x-row group), or null to copy plane by plane.
 // TC (float, one warp per block): the x-row sums of every stage on the tensor cores.
-template <class L1, int N, class T, int W, bool FixedX, bool Coherent, bool TC = false>
+// Ident: the caller's plane order is the library's (no plane table lookups on the stores).
+template <class L1, int N, class T, int W, bool FixedX, bool Coherent, bool TC = false, bool Ident = false>
 SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, const T *__restrict__ fin,
                           T *__restrict__ fout, int tile_index, T *buf, unsigned long long *full,
                           unsigned long long *empty, unsigned nt, const CUtensorMap *tm) {
@@ -827,7 +827,12 @@ SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, c
     const int dst_off = int(cs - g_al);
     const unsigned long long u0 = (unsigned long long)nt * (S::kTotal / NS);  // earlier uses of each buffer
     // caller plane of library population i
-    auto plane = [&](int i) -> long long { return a.identity ? i : __ldg(a.plane_idx + i); };
+    auto plane = [&](int i) -> long long {
+        if constexpr (Ident)
+            return i;
+        else
+            return __ldg(a.plane_idx + i);
+    };
     // warp 0: bit b of pending says buffer b has a fill issued and not yet waited for, bit b of
     // fpar is that fill's phase parity
     unsigned pending = 0u, fpar = 0u;
@@ -1010,7 +1015,7 @@ SMRT_D void tp_block_setup(unsigned char *dyn, unsigned long long *&full, unsign
 // One step: block b (W warps) takes the block tile b.
 // maps: tensor maps of the two states, used when a.tma is set (and the dynamic shared memory
 // is 128-byte aligned, as the boxes need).
-template <class L1, int N, class T, int W, bool FixedX, bool TC = false>
+template <class L1, int N, class T, int W, bool FixedX, bool TC = false, bool Ident = false>
 __global__ void __launch_bounds__(128) tp_step_line_block(TPArgs<T> a, int ntiles, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T, false> s;
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -1021,12 +1026,12 @@ __global__ void __launch_bounds__(128) tp_step_line_block(TPArgs<T> a, int ntile
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const CUtensorMap *tm = (a.tma && (smem_addr(dyn) & 127u) == 0u) ? &maps.src : nullptr;
-    tp_block_tile<L1, N, T, W, FixedX, false, TC>(a, s, a.fin, a.fout, t, buf, full, empty, 0u, tm);
+    tp_block_tile<L1, N, T, W, FixedX, false, TC, Ident>(a, s, a.fin, a.fout, t, buf, full, empty, 0u, tm);
 }
 
 // All nsteps steps in one cooperative launch (see step_line_persistent in kernels.cuh); the
 // blocks stride over the block tiles.
-template <class L1, int N, class T, int W, bool FixedX, bool TC = false>
+template <class L1, int N, class T, int W, bool FixedX, bool TC = false, bool Ident = false>
 __global__ void __launch_bounds__(128) tp_step_line_persistent_block(TPArgs<T> a, int nsteps, int ntiles,
                                                                      unsigned *barg, const __grid_constant__ TPMaps maps) {
     __shared__ TPTables<L1, T, false> s;
@@ -1048,7 +1053,7 @@ __global__ void __launch_bounds__(128) tp_step_line_persistent_block(TPArgs<T> a
         const CUtensorMap *tm = use_tma ? (src == a.fin ? &maps.src : &maps.dst) : nullptr;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             if (*static_cast<volatile int *>(&failed)) break;  // another warp gave up
-            if (!tp_block_tile<L1, N, T, W, FixedX, true, TC>(a, s, src, dst, t, buf, full, empty, nt, tm)) {
+            if (!tp_block_tile<L1, N, T, W, FixedX, true, TC, Ident>(a, s, src, dst, t, buf, full, empty, nt, tm)) {
                 failed = 1;
                 break;
             }

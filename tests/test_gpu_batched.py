@@ -140,6 +140,14 @@ def test_autotune_and_schedule_cache(lat, tmp_path):
     assert s2 == s1 and P.lb_get_schedule(ctx)["persistent"] == s1["persistent"]
     out = P.lb_step(ctx, f0.clone(), ctx.new_state(), 11)
     assert P.lb_poll_status(ctx)[0] == 0 and torch.isfinite(out).all()
+    # the persistent-only choice (what lb_step_graph replays) is cached under its own key
+    s3 = tuned_schedule(ctx, f0, LENGTHS, trial_steps=4, path=path, persistent=True)
+    assert s3["persistent"] == 1 and P.lb_get_schedule(ctx)["persistent"] == 1
+    assert tuned_schedule(ctx, f0, LENGTHS, trial_steps=4, path=path, persistent=True) == s3
+    assert tuned_schedule(ctx, f0, LENGTHS, trial_steps=6, path=path) == s1
+    a, b = f0.clone(), ctx.new_state()
+    g = P.lb_step_graph(ctx, a, b, 5)
+    assert P.lb_poll_status(ctx)[0] == 0 and torch.isfinite(g).all()
 
 
 def test_persistent_barrier_timeout_is_reported_and_recoverable(lat):
