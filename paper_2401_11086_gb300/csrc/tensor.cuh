@@ -648,6 +648,18 @@ struct TPCell {
 SMRT_D void mbar_arrive(unsigned long long *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
 }
+// One element global -> shared by an asynchronous copy (4 or 8 bytes, element-aligned) ...
+template <class T>
+SMRT_D void cp_async_elem(T *dst, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(int(sizeof(T)))
+                 : "memory");
+}
+// ... and the phase of mbarrier b waits for every such copy this thread has issued (the
+// barrier's pending count is raised now and lowered when they complete).
+SMRT_D void cp_async_mbar_arrive(unsigned long long *b) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
 
 // ------------------------------------------------------------------ block-staged line tile
 // A block of W warps owns a tile of 32 W consecutive cells of one line (warp w takes cells
@@ -674,7 +686,10 @@ struct TPBlockStage {
     // a stage buffer holds two groups of d rows (the +e_b and -e_b x-rows), each group
     // starting 128-byte aligned so that one tensor-map box fills it
     static constexpr int kGrp = int((L1::Q1 * kSeg * sizeof(T) + 127) / 128 * 128 / sizeof(T));
-    static constexpr int kStage = 2 * kGrp;             // elements per stage buffer
+    // then the end-state populations of the stage's planes, [left, right][2 d], for the pulls
+    // from beyond a line's fixed ends
+    static constexpr int kGhost = int((4 * L1::Q1 * sizeof(T) + 127) / 128 * 128 / sizeof(T));
+    static constexpr int kStage = 2 * kGrp + kGhost;    // elements per stage buffer
     static constexpr int kPerZ = L1::NP1 + 1;           // stages per z-plane
     static constexpr int kTotal = L1::Q1 * kPerZ;       // stages per step
     static_assert(kTotal % kStages == 0, "each tile starts the buffers' cycle at buffer 0");
@@ -826,6 +841,10 @@ SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, c
     const unsigned nbytes = unsigned((ce - cs) * (long long)sizeof(T));
     const int dst_off = int(cs - g_al);
     const unsigned long long u0 = (unsigned long long)nt * (S::kTotal / NS);  // earlier uses of each buffer
+    // does any pull of the tile come from beyond the left / right fixed end (block-uniform)?
+    const int xmax = (x0 + 32 * W < L ? x0 + 32 * W : L) - 1;
+    const bool needL = FixedX && x0 - EM - kx < 0;
+    const bool needR = FixedX && xmax + EM - kx >= L;
     // caller plane of library population i
     auto plane = [&](int i) -> long long {
         if constexpr (Ident)
@@ -850,6 +869,16 @@ SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, c
         T *sbuf = buf + size_t(sb) * S::kStage;
         if constexpr (Coherent) fence_async_global();
         fence_async_shared();
+        if (needL || needR) {  // the stage's end-state populations ride along with its fill
+            T *gs = sbuf + 2 * S::kGrp;
+            const int i0 = cz * P2 + k0;
+            for (int k = lane; k < nplanes; k += 32) {
+                if (needL) cp_async_elem(gs + k, gl + i0 + k);
+                if (needR) cp_async_elem(gs + 2 * Q1 + k, gr + i0 + k);
+            }
+            cp_async_mbar_arrive(b);
+            __syncwarp();  // before lane 0's arrival below can complete the phase
+        }
         if (tm) {  // one box per row group: d planes (library order) x SEG elements from g_al
             if (lane == 0) {
                 mbar_arrive_expect_tx(b, unsigned(nplanes) * unsigned(SEG * sizeof(T)));
@@ -914,12 +943,12 @@ SMRT_D bool tp_block_tile(const TPArgs<T> &a, const TPTables<L1, T, false> &s, c
                 if ((beyond >> av) & 1u) {
                     const int t = x - e1<L1>(av) - kx;
                     for (int r = 0; r < nrows; ++r) {
-                        const int i = cz * P2 + k0 + r * Q1 + av;
                         T v;
-                        if constexpr (FixedX)
-                            v = t < 0 ? gl[i] : gr[i];
+                        if constexpr (FixedX)  // the end state's population, staged with the fill
+                            v = bs[2 * S::kGrp + (t < 0 ? 0 : 2 * Q1) + r * Q1 + av];
                         else
-                            v = load_pop<Coherent>(fin + plane(i) * a.stride + base + wrap(t, L));
+                            v = load_pop<Coherent>(fin + plane(cz * P2 + k0 + r * Q1 + av) * a.stride + base +
+                                                   wrap(t, L));
                         bs[r * S::kGrp + av * SEG + tb - e1<L1>(av)] = v;
                     }
                 }
