@@ -202,12 +202,14 @@ print(json.dumps(bench.oracle_sample_rate({block}, {steps}, {warmup})))
 
 # The other workloads, each timed by its own bench.py run after the box on the same GPU (one
 # GPU only), reported in the box line under "secondary": the 64 batched shocks on D3Q103 in the
-# split precision, the 512 Table 3 shocks on D3Q729 in FP32, and the mixed-Mach batch (Ma 1.2 to
-# 7 on D3Q729 / D3Q4913) as one graph replay of 1000 steps per set.
+# split precision, the 512 Table 3 shocks on D3Q729 in FP32, the mixed-Mach batch (Ma 1.2 to 7 on
+# D3Q729 / D3Q4913) as one graph replay of 1000 steps per set, and the adjoint (its step kernel
+# on the batched shocks; the 5000-step differentiable shock forward and backward).
 SECONDARY_WORKLOADS = [
     ["--workload", "batched", "--steps", "200", "--warmup", "5"],
     ["--workload", "table3", "--precision", "f32", "--steps", "100", "--warmup", "5"],
     ["--workload", "mixed_mach", "--steps", "1000", "--warmup", "3"],
+    ["--workload", "adjoint", "--steps", "5000", "--warmup", "3"],
 ]
 
 
@@ -649,6 +651,107 @@ def run_mixed_mach(args, world: int, rank: int, local: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, world: int, rank: int, local: int) -> None:
+    """The reverse mode of the step (lb_step_adjoint, Sec. 3's collision and the streaming
+    transposed; FP64 adjoint arithmetic on the FP32 forward states of the split precision):
+    (1) the adjoint step kernel alone on the 64 batched D3Q103, N = 4 shocks, one launch per
+    step, its HBM roofline counting the forward state read in float and the adjoint state read
+    and written in double; (2) the differentiable shock (Ma = 5, 1024 cells, D3Q103, N = 4,
+    tanh width 10, K steps, a checkpoint every 250): one checkpointed forward run and its
+    backward pass through torch.autograd (relaxation_run), timed end to end: the loss is the
+    squared distance of the final rho, theta and q_x profiles to a run at the Table 4 times, the
+    start every time perturbed by up to +-20 % by seed."""
+    import numpy as np
+    import torch
+
+    import paper_2401_11086_gb300 as P
+    import synthetic
+    from paper_2401_11086_gb300 import shocks
+    from paper_2401_11086_gb300.autograd import relaxation_run
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    d = P.lb_lattice_named("D3Q103")
+    q = int(d.q)
+    stream = torch.cuda.current_stream()
+    # (1) the adjoint step kernel on the batched shocks
+    machs, lengths = batched_instances(rank)
+    ctx, f0, params = shocks.setup_batch(d, 4, machs, lengths, precision="f32c64", stream=stream)
+    cells = int(sum(lengths))
+    gen = torch.Generator(device=f0.device).manual_seed(synthetic.SEED + rank)
+    lam = 1e-3 * torch.randn(ctx.state_elems, dtype=torch.float64, device=f0.device, generator=gen)
+    lam2 = torch.empty_like(lam)
+    dtau = torch.zeros(len(params[0]["taus"]), dtype=torch.float64, device=f0.device)
+    for _ in range(args.warmup):
+        P.lb_step_adjoint(ctx, f0, lam, lam2, dtau)
+        lam, lam2 = lam2, lam
+    KA = args.adjoint_steps
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(KA):
+        P.lb_step_adjoint(ctx, f0, lam, lam2, dtau)
+        lam, lam2 = lam2, lam
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if P.lb_poll_status(ctx)[0] != 0 or not bool(torch.isfinite(lam).all()):
+        raise SystemExit("adjoint steps: health word or non-finite adjoint state")
+    kern_ms = ms / KA
+    rate, ms = job_rate(cells * q * KA, ms, dist)
+    # (2) the differentiable shock, forward and backward, end to end
+    K = args.steps
+    ctx1, h0, p1 = shocks.setup_batch(d, 4, [5.0], [1024], precision="f32c64", width=10.0, stream=stream)
+    P.lb_set_relaxation(ctx1, p1[0]["taus"], True, 1.0, p1[0]["left"], p1[0]["right"])
+    taus_ref = np.asarray(p1[0]["taus"], dtype=np.float64)
+    with torch.no_grad():
+        tgt = relaxation_run(ctx1, torch.tensor(taus_ref), h0, K, checkpoint_every=250).clone()
+    tau = torch.tensor(synthetic.perturbed(taus_ref, 0.2, seed=synthetic.SEED + rank), requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = relaxation_run(ctx1, tau, h0, K, checkpoint_every=250)
+    loss = ((out - tgt) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    run_ms = (time.perf_counter() - t0) * 1e3
+    grad_ok = bool(torch.isfinite(tau.grad).all()) and P.lb_poll_status(ctx1)[0] == 0
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak()
+    alg_bytes = float(cells) * q * (4 + 8 + 8)
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": rate / 1e9, "unit": UNIT, "n_gpus": world, "steps": KA,
+            "warmup": args.warmup, "ms_per_step": ms / KA, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 adjoint of f32 forward states (exact fixed-point sums)",
+            "data": "synthetic",
+            "config": {"workload": "adjoint_step_batched_shocks_64_d3q103_n4", "instances_per_gpu": len(machs),
+                       "cells_per_gpu": cells, "velocities": q, "hermite_order": 4,
+                       "schedule": P.lb_get_schedule(ctx),
+                       "l2": "inputs larger than L2 (81 MB forward state, two 162 MB adjoint states)",
+                       "differentiable_shock": {
+                           "workload": "differentiable_shock_ma5_1024_d3q103_n4_f32c64", "steps": K,
+                           "checkpoint_every": 250, "ms_forward_and_backward": run_ms,
+                           "ms_per_differentiated_step": run_ms / K,
+                           "launches": "K forward steps, K - K/250 recomputed, K adjoint steps, one "
+                                       "launch each (1024 cells: launch-latency bound)",
+                           "gradient_finite": grad_ok}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": kern_ms,
+                         "note": "forward state read in float, adjoint state read and written in double"},
+            "cpu_baseline": None, "gpu_launches": KA, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_convergence(args, rank: int, local: int) -> None:
     """The Appendix B study: smallest Hermite order of the 1D Maxwellian's expansion with L1
     error below 0.01, on a 200 x 200 grid of theta in [0.1, 2] and u in [0, 4], orders <= 99."""
@@ -725,10 +828,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="box workload: skip the other workloads' runs reported under 'secondary'")
-    ap.add_argument("--workload", default="box", choices=["box", "batched", "table3", "convergence", "mixed_mach"],
+    ap.add_argument("--workload", default="box",
+                    choices=["box", "batched", "table3", "convergence", "mixed_mach", "adjoint"],
                     help="box: the 256^3 roofline case (default); batched: 64 1D shocks on "
                          "D3Q103; table3: 512 Table 3 shocks on D3Q729, N = 5; convergence: the "
-                         "Appendix B study; mixed_mach: 64 shocks with Ma in [1.2, 7] on D3Q729 / "
+                         "Appendix B study; adjoint: the adjoint step on the batched shocks and the "
+                         "differentiable shock; mixed_mach: 64 shocks with Ma in [1.2, 7] on D3Q729 / "
                          "D3Q4913, K steps in one graph-captured persistent launch per set")
     ap.add_argument("--es-b", type=float, default=None,
                     help="table3 workload: run the ES-BGK model with this b instead of SMRT")
@@ -739,6 +844,8 @@ def main():
                     help="table3 workload: the D3Q729 rows (Ma 1.5/3/5) or the D3Q4913 row (Ma 7)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="table3 workload, f32: the projection's x-row sums on the tensor cores")
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="adjoint workload: timed adjoint steps on the batched shocks")
     ap.add_argument("--tile-width", type=int, default=0,
                     help="table3 workload: block tile width (32, 64, 128; 0: the library's default)")
     ap.add_argument("--length", type=int, default=0,
@@ -755,6 +862,9 @@ def main():
         return
     if args.impl == "ours" and args.workload == "table3":
         run_table3(args, world, rank, local)
+        return
+    if args.impl == "ours" and args.workload == "adjoint":
+        run_adjoint(args, world, rank, local)
         return
     if args.impl == "ours" and args.workload == "mixed_mach":
         run_mixed_mach(args, world, rank, local)
