@@ -182,7 +182,8 @@ lb_status lb_step(lb_ctx *ctx, void *f_a, void *f_b, int nsteps);
 
 /* Launch schedule of the 1D-line (batched) kernels. tile_width: cells per block (32, 64, 128;
  * on D3Q729 and D3Q4913 a block of tile_width / 32 warps steps a tile of tile_width cells whose
- * pulls it stages once for all its warps, one 32-cell row per warp; on D3Q729 the value
+ * pulls it stages once for all its warps, one 32-cell row per warp -- lb_init_lattice sets 128
+ * for LB_F32, 32 (D3Q729) or 64 (D3Q4913) for LB_F64, 128 on the other sets; on D3Q729 the value
  * 1 selects one block per cell -- its populations in shared memory, the factored sums spread
  * over the block -- which lb_init_lattice picks for problems of at most 48 (LB_F64) or 32 (LB_F32)
  * cells per SM, and
