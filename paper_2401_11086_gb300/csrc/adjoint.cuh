@@ -232,31 +232,68 @@ struct AdjMath : AdjMoments<Nm> {
     static constexpr int NP = Lat::NP;
     static constexpr int M = nmom(Nm);
 
-    // F1: Rc_g = c^|g| sum_i x_i e_i^g  (x in library order; pairs folded)
-    SMRT_HD static void raw(const double (&x)[Q], double c, double (&Rc)[M]) {
-        double S[NP], D[NP];
-        static_for<NP>([&](auto P) {
-            constexpr int p = decltype(P)::value;
-            S[p] = x[2 * p + 1] + x[2 * p + 2];
-            D[p] = x[2 * p + 1] - x[2 * p + 2];
+    // The contractions run per sign orbit of the velocity set (lattices.cuh): a monomial sum over
+    // an orbit is a^gamma times one entry of a Walsh-Hadamard transform of its pair sums (even
+    // |gamma|) or differences (odd |gamma|), and the transposed contraction is the same
+    // transform of per-parity-class sums; a quarter of the multiply-adds of a pair-by-pair sum
+    // on the 8-member orbits.
+    static constexpr SignOrbits<Lat> kOrb = SignOrbits<Lat>();
+
+    // unnormalised Walsh-Hadamard transform of NB = 1, 2 or 4 values in place:
+    // x_out[c] = sum_b (-1)^popcount(b & c) x_in[b]
+    template <int NB>
+    SMRT_HD static void wht_d(double (&x)[NB]) {
+        static_for<(NB >= 4 ? 2 : (NB >= 2 ? 1 : 0))>([&](auto Tt) {
+            constexpr int bit = 1 << decltype(Tt)::value;
+            static_for<NB>([&](auto Bb) {
+                constexpr int bb = decltype(Bb)::value;
+                if constexpr ((bb & bit) == 0) {
+                    const double lo = x[bb], hi = x[bb | bit];
+                    x[bb] = lo + hi;
+                    x[bb | bit] = lo - hi;
+                }
+            });
         });
-        double cp = 1.0;
+    }
+
+    // F1: Rc_g = c^|g| sum_i x_i e_i^g  (x in library order)
+    SMRT_HD static void raw(const double (&x)[Q], double c, double (&Rc)[M]) {
         double cpow[Nm + 1];
+        double cp = 1.0;
         static_for<Nm + 1>([&](auto J) {
             cpow[decltype(J)::value] = cp;
             cp *= c;
         });
+        static_for<M>([&](auto G) { Rc[decltype(G)::value] = 0.0; });
+        Rc[0] = x[0];
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            double S[np], D[np];
+            static_for<np>([&](auto B) {
+                constexpr int bb = decltype(B)::value, p = kOrb.pair[o][bb];
+                constexpr bool fl = kOrb.flip[o][bb] != 0;
+                const double fp = x[2 * p + 1], fm = x[2 * p + 2];
+                S[bb] = fp + fm;
+                D[bb] = fl ? fm - fp : fp - fm;
+            });
+            wht_d<np>(S);
+            wht_d<np>(D);
+            static_for<M>([&](auto G) {
+                constexpr int g = decltype(G)::value;
+                constexpr int m = kOrb.monomial(o, g);
+                if constexpr (m != 0) {
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        Rc[g] += double(m) * S[cl];
+                    else
+                        Rc[g] += double(m) * D[cl];
+                }
+            });
+        });
         static_for<M>([&](auto G) {
             constexpr int g = decltype(G)::value;
-            constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-            constexpr bool even = ((g0 + g1 + g2) & 1) == 0;
-            double acc = (g == 0) ? x[0] : 0.0;
-            static_for<NP>([&](auto Pp) {
-                constexpr int p = decltype(Pp)::value;
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
-                if constexpr (m != 0) acc += double(m) * (even ? S[p] : D[p]);
-            });
-            Rc[g] = acc * cpow[mi_order(g)];
+            if constexpr (mi_order(g) > 0) Rc[g] *= cpow[mi_order(g)];
         });
     }
 
@@ -271,25 +308,36 @@ struct AdjMath : AdjMoments<Nm> {
         });
         static_for<M>([&](auto G) { sc[decltype(G)::value] = Rcb[decltype(G)::value] * cpow[mi_order(decltype(G)::value)]; });
         xb[0] += sc[0];
-        static_for<NP>([&](auto Pp) {
-            constexpr int p = decltype(Pp)::value;
-            double ev = 0.0, od = 0.0;
+        static_for<kOrb.n>([&](auto O) {
+            constexpr int o = decltype(O)::value;
+            constexpr int np = 1 << (kOrb.k[o] - 1);
+            double E[np], Od[np];
+            static_for<np>([&](auto B) {
+                E[decltype(B)::value] = 0.0;
+                Od[decltype(B)::value] = 0.0;
+            });
             static_for<M>([&](auto G) {
                 constexpr int g = decltype(G)::value;
-                constexpr int g0 = mi_comp(g, 0), g1 = mi_comp(g, 1), g2 = mi_comp(g, 2);
-                constexpr int m = ipow(Lat::e(p, 0), g0) * ipow(Lat::e(p, 1), g1) * ipow(Lat::e(p, 2), g2);
+                constexpr int m = kOrb.monomial(o, g);
                 if constexpr (m != 0) {
-                    if constexpr (((g0 + g1 + g2) & 1) == 0)
-                        ev += double(m) * sc[g];
+                    constexpr int cl = kOrb.parity_class(o, g);
+                    if constexpr ((mi_order(g) & 1) == 0)
+                        E[cl] += double(m) * sc[g];
                     else
-                        od += double(m) * sc[g];
+                        Od[cl] += double(m) * sc[g];
                 }
             });
-            xb[2 * p + 1] += ev + od;
-            xb[2 * p + 2] += ev - od;
+            wht_d<np>(E);  // the even and odd parts of the sum at each member of the orbit
+            wht_d<np>(Od);
+            static_for<np>([&](auto B) {
+                constexpr int bb = decltype(B)::value, p = kOrb.pair[o][bb];
+                constexpr bool fl = kOrb.flip[o][bb] != 0;
+                const double vplus = E[bb] + Od[bb], vminus = E[bb] - Od[bb];
+                xb[2 * p + 1] += fl ? vminus : vplus;
+                xb[2 * p + 2] += fl ? vplus : vminus;
+            });
         });
     }
-
 };
 
 // Conserved moments from the raw moments (F2) and the transpose of F2 (onto Rcb).
