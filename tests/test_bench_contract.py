@@ -1,6 +1,6 @@
 """bench.py's host logic on the CPU: the reference arm's JSON line (the oracle timed on the host
-cores) and the rule that a committed ncu figure is reported only while the kernel sources it
-was taken on are unchanged."""
+cores), the rule that a committed ncu figure is reported only while the kernel sources it was
+taken on are unchanged, and the secondary workloads of the default run."""
 import json
 import os
 import subprocess
@@ -38,3 +38,20 @@ def test_profile_figures_follow_the_kernel_sources(tmp_path):
     p.write_text("kernel_sources_sha256_12: 000000000000\ndram_bytes_per_cell: 289.3\n")
     assert bench.profile_value(str(p), "dram_bytes_per_cell") is None
     assert bench.profile_value(str(tmp_path / "absent.txt"), "dram_bytes_per_cell") is None
+
+
+def test_committed_profiles_match_the_kernel_sources():
+    """The box and batched summaries under profiles/ were captured on the kernels as committed,
+    so the bench line reports their DRAM traffic (it would print null after a kernel edit)."""
+    assert bench.profile_traffic(256) is not None
+    assert bench.profile_value(bench.PROFILE_BATCHED, "dram_bytes_per_launch") is not None
+
+
+def test_secondary_workloads_parse_and_failures_are_reported():
+    """Every secondary workload is a valid bench.py command line, and a child that fails is
+    reported in the box line instead of ending the run."""
+    for extra in bench.SECONDARY_WORKLOADS:
+        assert extra[0] == "--workload" and extra[1] in ("batched", "table3", "mixed_mach", "adjoint")
+        assert int(extra[extra.index("--steps") + 1]) > 0 and int(extra[extra.index("--warmup") + 1]) >= 3
+    out = bench.run_secondary(["--workload", "no_such_workload"], timeout=120)
+    assert out["args"] == "--workload no_such_workload" and "error" in out and "value" not in out
